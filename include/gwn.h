@@ -1,0 +1,195 @@
+/*
+ * gwn.h -- C ABI of the GB300 generalized-winding-number (GWN) library.
+ *
+ * The library answers batched containment queries against collections of
+ * NURBS curves (2D) and trimmed NURBS patches (3D) with the agglomerated
+ * evaluation of "Spatially Accelerated Winding Numbers for Curved Geometry"
+ * (Algorithm 1): adaptive subdivision (Section 3.2), uncentred moments summed
+ * up a Karras LBVH and centred in place (Section 3.1, Eq. 3 and the moment
+ * transform), and a per-query traversal that evaluates the order-0/1/2 Taylor
+ * expansion of Eq. 3 for clusters that pass the far test of Section 3 and the
+ * exact GWN (Section 3.3) for the leaves it reaches.
+ *
+ * Conventions shared by every call
+ *   - Every function returns gwn_status; nothing throws across the ABI.
+ *     gwn_last_error() returns a thread-local message for the last failure.
+ *   - GWN normalisation follows Eq. 2: a counter-clockwise closed curve, or a
+ *     closed shell with outward normals S_u x S_v, has winding number 1 inside.
+ *   - Curves and patches use clamped knot vectors (first and last knot repeated
+ *     degree + 1 times), positive weights, and degree 1..3 in each direction.
+ *   - Trimming curves of a patch are closed loops in its (u, v) domain; the
+ *     visible region is counted with the loops' winding number (outer loops
+ *     counter-clockwise, holes clockwise).  A patch with n_trims == 0 is
+ *     untrimmed: its boundary is the parameter rectangle.
+ *   - A gwn_model owns all device memory it allocates until gwn_release();
+ *     the build functions deep-copy their inputs, so the caller may free them
+ *     when the call returns.  Output buffers always belong to the caller.
+ */
+#ifndef GWN_H
+#define GWN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GWN_OK = 0,
+    GWN_ERR_INVALID_ARG = 1,      /* bad pointer, size, option or unsupported degree */
+    GWN_ERR_INVALID_GEOMETRY = 2, /* non-clamped knots, weights <= 0, NaN/Inf, trims outside the domain */
+    GWN_ERR_OOM = 3,              /* device or host allocation failed */
+    GWN_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+    GWN_ERR_TIMEOUT = 5,          /* a bounded device or host wait ran out */
+    GWN_ERR_BUSY = 6,             /* not admitted yet (memory budget); retry later */
+    GWN_ERR_INTERNAL = 7,
+    GWN_ERR_NOT_FOUND = 8         /* unknown request or model id */
+} gwn_status;
+
+typedef struct gwn_model_s* gwn_model;
+
+/* A NURBS curve in the plane.  ctrl: n_ctrl x 2 (x, y), weights: n_ctrl or
+ * NULL (all ones), knots: n_ctrl + degree + 1, clamped and non-decreasing. */
+typedef struct {
+    int32_t degree;
+    int32_t n_ctrl;
+    const double* ctrl;
+    const double* weights;
+    const double* knots;
+} gwn_curve2d;
+
+/* A trimmed tensor-product NURBS patch.  ctrl: n_u x n_v x 3 with the v index
+ * fastest ((i_u * n_v + i_v) * 3), weights: n_u x n_v or NULL, knots_u:
+ * n_u + deg_u + 1, knots_v: n_v + deg_v + 1.  trims: n_trims curves in (u, v)
+ * that must lie inside the parameter rectangle. */
+typedef struct {
+    int32_t deg_u, deg_v;
+    int32_t n_u, n_v;
+    const double* ctrl;
+    const double* weights;
+    const double* knots_u;
+    const double* knots_v;
+    int32_t n_trims;
+    const gwn_curve2d* trims;
+} gwn_patch3d;
+
+enum {
+    GWN_PREC_FP32_REPAIR = 0, /* FP32 traversal, FP64 re-evaluation near half-integers and for flagged queries */
+    GWN_PREC_FP32 = 1,        /* FP32 only (no repair) */
+    GWN_PREC_FP64 = 2         /* every query evaluated in FP64 */
+};
+
+enum {
+    GWN_MODE_BVH = 0,    /* Algorithm 1: LBVH traversal with Taylor far field */
+    GWN_MODE_DIRECT = 1  /* plain direct sum: every leaf evaluated exactly for every query */
+};
+
+enum { GWN_F32 = 0, GWN_F64 = 1 };              /* point dtypes */
+enum { GWN_DEVICE_HOST_ONLY = -2 };
+enum { GWN_MEM_DEVICE = 0, GWN_MEM_HOST = 1 };  /* where points and outputs live */
+
+/* Per-query status bits written to out_status. */
+enum {
+    GWN_QS_REPAIRED = 1u,       /* value re-evaluated in FP64 */
+    GWN_QS_NEAR = 2u,           /* a leaf needed its deepest refinement level (query very near the boundary) */
+    GWN_QS_STACK_OVERFLOW = 4u, /* traversal stack overflow in the FP32 pass (value repaired) */
+    GWN_QS_UNRESOLVED = 8u      /* FP64 pass also hit a refinement or stack limit: value may be inexact */
+};
+
+typedef struct {
+    double tolerance;     /* target max |dGWN| for the FP32 path (default 1e-4) */
+    double max_aabb_frac; /* subdivide until a leaf's box diagonal < frac * shape diagonal (0.1); <= 0: no subdivision */
+    int32_t order;        /* Taylor order 0, 1 or 2 (default 2) */
+    double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2 (default 2) */
+    double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves (default 0) */
+    double repair_band;   /* re-evaluate in FP64 when |w - round(w) +- 1/2| < band (default 1e-3) */
+    int32_t quad_nodes;   /* Gauss-Legendre nodes per rule for 3D moments (default 10) */
+    int32_t precision;    /* GWN_PREC_* (default GWN_PREC_FP32_REPAIR) */
+    int32_t device;       /* CUDA device ordinal, -1 = current (default -1); GWN_DEVICE_HOST_ONLY
+                             builds the host-side tree only (inspection, no queries) */
+    int32_t n_threads;    /* host threads for the build, 0 = all (default 0) */
+} gwn_build_opts;
+
+/* Fills *opts with the defaults listed above. */
+void gwn_default_build_opts(gwn_build_opts* opts);
+
+typedef struct {
+    int32_t mode;      /* GWN_MODE_* (default GWN_MODE_BVH) */
+    int32_t precision; /* GWN_PREC_*, or -1 = the model's (default -1) */
+    double beta;       /* 0 = the model's */
+} gwn_query_opts;
+
+void gwn_default_query_opts(gwn_query_opts* opts);
+
+/* Build a 2D model from n NURBS curves (Algorithm 1, preprocessing):
+ * Bezier extraction and adaptive subdivision (Section 3.2), chord moments
+ * (Section 3.1: far from a curve its GWN equals that of its chord), LBVH
+ * (Section 3.1, Karras), moment up-sweep and centring.  On success *out holds
+ * a device-resident model.  Errors: INVALID_ARG, INVALID_GEOMETRY, OOM, CUDA. */
+gwn_status gwn_build_2d(const gwn_curve2d* curves, size_t n, const gwn_build_opts* opts, gwn_model* out);
+
+/* Build a 3D model from n trimmed NURBS patches (Algorithm 1,
+ * preprocessing): adaptive subdivision of the parameter rectangle with trims
+ * clipped to every leaf (Section 3.2), leaf moments and centroid by
+ * Gauss-Legendre quadrature over the trimmed region via Green's theorem
+ * (Section 3.1, Figure 3), LBVH, up-sweep and centring.  Same errors. */
+gwn_status gwn_build_3d(const gwn_patch3d* patches, size_t n, const gwn_build_opts* opts, gwn_model* out);
+
+/* GWN at n points (Algorithm 1, batched query).
+ *   points    : n x 2 (2D model) or n x 3 (3D model), dtype GWN_F32 or GWN_F64
+ *   mem       : GWN_MEM_DEVICE -- points and outputs are device pointers and the
+ *               call is asynchronous on `stream`; GWN_MEM_HOST -- host pointers,
+ *               staged through model-owned device buffers, synchronous.
+ *   out_w     : n doubles (required); out_label: n int32 = round(w) (nullable);
+ *   out_status: n uint32 GWN_QS_* bits (nullable).
+ *   stream    : a cudaStream_t, or NULL for the default stream.
+ * Concurrent calls on the same model must be serialised by the caller (the
+ * model's scratch buffers are shared).  n == 0 is a no-op. */
+gwn_status gwn_query(gwn_model model, const void* points, int32_t points_dtype, int32_t mem, size_t n,
+                     double* out_w, int32_t* out_label, uint32_t* out_status, const gwn_query_opts* qopts,
+                     void* stream);
+
+typedef struct {
+    int32_t dim;
+    int64_t n_primitives;   /* curves or patches given to the build */
+    int64_t n_leaves;       /* after Bezier extraction and subdivision */
+    int64_t n_nodes;        /* internal nodes = n_leaves - 1 */
+    int32_t max_depth;      /* deepest leaf */
+    int64_t device_bytes;   /* device memory owned by the model */
+    double build_ms;        /* wall time of the build */
+    double beta, beta_repair, repair_band;
+    int32_t order;
+    double lo[3], hi[3];    /* box of all control points */
+} gwn_model_stats;
+
+gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
+
+/* Copy per-leaf records to host memory for inspection (used by the tests).
+ * For each leaf i in BVH order: prim[i] = input primitive index and
+ * param[4 i .. 4 i + 3] = (t0, t1, 0, 0) for curves or (u0, u1, v0, v1) for
+ * patches.  Either pointer may be NULL; arrays hold n_leaves entries. */
+gwn_status gwn_model_leaves(gwn_model model, int64_t* prim, double* param);
+
+/* Copy the FP64 tree to host memory (used by the tests): for internal node k,
+ * child[2k], child[2k+1] (>= 0: internal node, < 0: leaf ~index), centroid
+ * x0[dim k ..], radius r[k], and the centred moments mom[k * M ..] with
+ * M = d + d^2 + d^3 laid out as m0[d], m1[d][d], m2[d][d][d] with
+ * m1_ij = int (x - x0)_i n_j and m2_ijk = int (x - x0)_i (x - x0)_j n_k.
+ * Any pointer may be NULL. */
+gwn_status gwn_model_tree(gwn_model model, int32_t* child, double* x0, double* r, double* mom);
+
+/* Release a model and all its device memory.  NULL is a no-op. */
+gwn_status gwn_release(gwn_model model);
+
+/* Thread-local description of the last error (never NULL). */
+const char* gwn_last_error(void);
+
+/* Library version string. */
+const char* gwn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWN_H */

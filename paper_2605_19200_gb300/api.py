@@ -1,0 +1,305 @@
+"""Python binding of the C ABI in include/gwn.h (argument marshalling only).
+
+Functions keep the C names (gwn_build_2d, gwn_query, ...).  Geometry comes in
+as synth-style objects with ``degree/ctrl/weights/knots`` (curves) and
+``deg_u/deg_v/ctrl/weights/knots_u/knots_v/trims`` (patches); points and
+outputs are torch tensors (device or host) or numpy arrays (host).  Every
+computation happens in libgwn.so; this module never evaluates a winding
+number itself.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import native
+
+GWN_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INVALID_GEOMETRY", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
+                6: "BUSY", 7: "INTERNAL", 8: "NOT_FOUND"}
+PREC_FP32_REPAIR, PREC_FP32, PREC_FP64 = 0, 1, 2
+MODE_BVH, MODE_DIRECT = 0, 1
+F32, F64 = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+QS_REPAIRED, QS_NEAR, QS_STACK_OVERFLOW, QS_UNRESOLVED = 1, 2, 4, 8
+
+
+class GwnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class gwn_curve2d(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("n_ctrl", ctypes.c_int32), ("ctrl", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("knots", ctypes.c_void_p)]
+
+
+class gwn_patch3d(ctypes.Structure):
+    _fields_ = [("deg_u", ctypes.c_int32), ("deg_v", ctypes.c_int32), ("n_u", ctypes.c_int32),
+                ("n_v", ctypes.c_int32), ("ctrl", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("knots_u", ctypes.c_void_p), ("knots_v", ctypes.c_void_p), ("n_trims", ctypes.c_int32),
+                ("trims", ctypes.c_void_p)]
+
+
+class gwn_build_opts(ctypes.Structure):
+    _fields_ = [("tolerance", ctypes.c_double), ("max_aabb_frac", ctypes.c_double), ("order", ctypes.c_int32),
+                ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double), ("repair_band", ctypes.c_double),
+                ("quad_nodes", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("n_threads", ctypes.c_int32)]
+
+
+class gwn_query_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double)]
+
+
+class gwn_model_stats(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_primitives", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("build_ms", ctypes.c_double), ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double),
+                ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "gwn_default_build_opts": (None, [ctypes.POINTER(gwn_build_opts)]),
+    "gwn_default_query_opts": (None, [ctypes.POINTER(gwn_query_opts)]),
+    "gwn_build_2d": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.POINTER(gwn_build_opts), ctypes.POINTER(_P)]),
+    "gwn_build_3d": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.POINTER(gwn_build_opts), ctypes.POINTER(_P)]),
+    "gwn_query": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t, _P, _P, _P,
+                                 ctypes.POINTER(gwn_query_opts), _P]),
+    "gwn_model_info": (ctypes.c_int, [_P, ctypes.POINTER(gwn_model_stats)]),
+    "gwn_model_leaves": (ctypes.c_int, [_P, _P, _P]),
+    "gwn_model_tree": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gwn_release": (ctypes.c_int, [_P]),
+    "gwn_last_error": (ctypes.c_char_p, []),
+    "gwn_version": (ctypes.c_char_p, []),
+}
+
+
+def lib() -> ctypes.CDLL:
+    L = native.load()
+    if not getattr(L, "_gwn_sigs", False):
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        L._gwn_sigs = True
+    return L
+
+
+def _check(code: int):
+    if code != GWN_OK:
+        raise GwnError(code, lib().gwn_last_error().decode())
+
+
+def default_build_opts(**kw) -> gwn_build_opts:
+    o = gwn_build_opts()
+    lib().gwn_default_build_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown build option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def default_query_opts(**kw) -> gwn_query_opts:
+    o = gwn_query_opts()
+    lib().gwn_default_query_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown query option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class _Pack:
+    """Contiguous float64 buffers that keep the ABI structs' pointers alive."""
+
+    def __init__(self):
+        self.parts = []
+        self.size = 0
+
+    def add(self, a) -> int:
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        off = self.size
+        self.parts.append(a)
+        self.size += a.size
+        return off
+
+    def finish(self):
+        self.buf = np.concatenate(self.parts) if self.parts else np.zeros(1)
+        self.base = self.buf.ctypes.data
+        return self.base
+
+
+def _curve_array(curves: Sequence, pack: _Pack):
+    arr = (gwn_curve2d * max(1, len(curves)))()
+    offs = []
+    for c in curves:
+        offs.append((pack.add(c.ctrl), pack.add(c.weights), pack.add(c.knots)))
+    return arr, offs
+
+
+def _fill_curves(arr, curves, offs, base):
+    for i, (c, (o1, o2, o3)) in enumerate(zip(curves, offs)):
+        arr[i].degree = int(c.degree)
+        arr[i].n_ctrl = int(c.ctrl.shape[0])
+        arr[i].ctrl = base + 8 * o1
+        arr[i].weights = base + 8 * o2
+        arr[i].knots = base + 8 * o3
+
+
+class Model:
+    """Owning wrapper of a gwn_model handle."""
+
+    def __init__(self, handle: int, dim: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.dim = dim
+
+    def release(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gwn_release(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        s = gwn_model_stats()
+        _check(lib().gwn_model_info(self.handle, ctypes.byref(s)))
+        return {f: (list(getattr(s, f)) if f in ("lo", "hi") else getattr(s, f)) for f, _ in s._fields_}
+
+    def leaves(self):
+        n = self.info()["n_leaves"]
+        prim = np.zeros(n, dtype=np.int64)
+        param = np.zeros((n, 4))
+        _check(lib().gwn_model_leaves(self.handle, prim.ctypes.data, param.ctypes.data))
+        return prim, param
+
+    def tree(self):
+        info = self.info()
+        ni, d = info["n_nodes"], self.dim
+        M = d + d * d + d ** 3
+        child = np.zeros((max(ni, 1), 2), dtype=np.int32)
+        x0 = np.zeros((max(ni, 1), d))
+        r = np.zeros(max(ni, 1))
+        mom = np.zeros((max(ni, 1), M))
+        _check(lib().gwn_model_tree(self.handle, child.ctypes.data, x0.ctypes.data, r.ctypes.data, mom.ctypes.data))
+        return {"child": child[:ni], "x0": x0[:ni], "r": r[:ni], "mom": mom[:ni]}
+
+    def query(self, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
+              want_label: bool = True, want_status: bool = True):
+        return gwn_query(self, points, mode=mode, precision=precision, beta=beta, stream=stream,
+                         want_label=want_label, want_status=want_status)
+
+
+def gwn_build_2d(curves: Sequence, opts: Optional[gwn_build_opts] = None, **kw) -> Model:
+    opts = opts or default_build_opts(**kw)
+    pack = _Pack()
+    arr, offs = _curve_array(curves, pack)
+    base = pack.finish()
+    _fill_curves(arr, curves, offs, base)
+    h = ctypes.c_void_p()
+    _check(lib().gwn_build_2d(ctypes.cast(arr, _P), len(curves), ctypes.byref(opts), ctypes.byref(h)))
+    return Model(h.value, 2)
+
+
+def gwn_build_3d(patches: Sequence, opts: Optional[gwn_build_opts] = None, **kw) -> Model:
+    opts = opts or default_build_opts(**kw)
+    pack = _Pack()
+    parr = (gwn_patch3d * max(1, len(patches)))()
+    poffs = []
+    trim_arrays = []
+    all_trims = []
+    for p in patches:
+        poffs.append((pack.add(p.ctrl), pack.add(p.weights), pack.add(p.knots_u), pack.add(p.knots_v)))
+        tarr, toffs = _curve_array(p.trims, pack)
+        trim_arrays.append(tarr)
+        all_trims.append(toffs)
+    base = pack.finish()
+    for i, p in enumerate(patches):
+        o1, o2, o3, o4 = poffs[i]
+        s = parr[i]
+        s.deg_u, s.deg_v = int(p.deg_u), int(p.deg_v)
+        s.n_u, s.n_v = int(p.ctrl.shape[0]), int(p.ctrl.shape[1])
+        s.ctrl, s.weights = base + 8 * o1, base + 8 * o2
+        s.knots_u, s.knots_v = base + 8 * o3, base + 8 * o4
+        s.n_trims = len(p.trims)
+        _fill_curves(trim_arrays[i], p.trims, all_trims[i], base)
+        s.trims = ctypes.cast(trim_arrays[i], _P).value if p.trims else None
+    h = ctypes.c_void_p()
+    _check(lib().gwn_build_3d(ctypes.cast(parr, _P), len(patches), ctypes.byref(opts), ctypes.byref(h)))
+    m = Model(h.value, 3)
+    return m
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
+              want_label: bool = True, want_status: bool = True):
+    """GWN at points.  torch CUDA tensor -> asynchronous device call with device
+    outputs; numpy array or CPU tensor -> host call (staged, synchronous).
+    Returns (w float64, label int32 or None, status uint32/int32 or None)."""
+    q = default_query_opts(mode=mode, precision=precision, beta=beta)
+    try:
+        import torch
+    except Exception:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(points, torch.Tensor) and points.is_cuda:
+        pts = points.contiguous()
+        if pts.dtype not in (torch.float32, torch.float64):
+            pts = pts.float()
+        n = pts.shape[0]
+        dt = F32 if pts.dtype == torch.float32 else F64
+        w = torch.empty(n, dtype=torch.float64, device=pts.device)
+        lab = torch.empty(n, dtype=torch.int32, device=pts.device) if want_label else None
+        st = torch.empty(n, dtype=torch.int32, device=pts.device) if want_status else None
+        _check(lib().gwn_query(model.handle, pts.data_ptr(), dt, MEM_DEVICE, n, w.data_ptr(),
+                               lab.data_ptr() if lab is not None else None,
+                               st.data_ptr() if st is not None else None, ctypes.byref(q),
+                               _stream_handle(stream)))
+        return w, lab, st
+    if torch is not None and isinstance(points, torch.Tensor):
+        points = points.numpy()
+    pts = np.ascontiguousarray(points)
+    if pts.dtype not in (np.float32, np.float64):
+        pts = pts.astype(np.float64)
+    n = pts.shape[0]
+    dt = F32 if pts.dtype == np.float32 else F64
+    w = np.zeros(n)
+    lab = np.zeros(n, dtype=np.int32) if want_label else None
+    st = np.zeros(n, dtype=np.uint32) if want_status else None
+    _check(lib().gwn_query(model.handle, pts.ctypes.data, dt, MEM_HOST, n, w.ctypes.data,
+                           lab.ctypes.data if lab is not None else None,
+                           st.ctypes.data if st is not None else None, ctypes.byref(q),
+                           _stream_handle(stream)))
+    return w, lab, st
+
+
+def gwn_model_info(model: Model) -> dict:
+    return model.info()
+
+
+def gwn_release(model: Model):
+    model.release()
+
+
+def gwn_version() -> str:
+    return lib().gwn_version().decode()

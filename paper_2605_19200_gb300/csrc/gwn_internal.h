@@ -1,0 +1,99 @@
+// gwn_internal.h -- data layouts shared by the host build and the CUDA kernels.
+//
+// A model is a Karras LBVH (Section 3.1) over leaf primitives.  Internal node k
+// (0 <= k < n_leaves - 1) stores its centroid x0 and squared radius r^2 (radius
+// = half the diagonal of the node's control-point box, Section 3), its two
+// children (>= 0: internal node, < 0: leaf ~i), and the order-2 Taylor
+// coefficients of Eq. 3 folded into the polynomial form evaluated by the
+// kernels (see fold_moments_2d / fold_moments_3d in build.cpp):
+//
+//   2D  w = i2 (A0.r + a1 + i2 (r^T B r + c.r + i2 D[r r r])),  i2 = 1/|r|^2
+//   3D  w = i3 (A0.r + a1 + i2 (r^T B r + c.r + i2 D[r r r])),  i3 = 1/|r|^3
+//
+// with r = x0 - q.  Every array is a structure of arrays indexed by node or
+// leaf so that a node visit reads one 16-byte header, and the moment block is
+// read only when the far test passes.
+#pragma once
+
+#include <cstdint>
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#else
+struct alignas(16) float4 { float x, y, z, w; };
+struct alignas(8) int2 { int x, y; };
+#endif
+
+namespace gwn {
+
+constexpr int kMom2Vec = 3;    // float4 per 2D moment block (12 floats)
+constexpr int kMom3Vec = 6;    // float4 per 3D moment block (23 floats + pad)
+constexpr int kMom2F64 = 12;   // doubles per 2D moment block
+constexpr int kMom3F64 = 24;   // doubles per 3D moment block
+// 2D leaf: cubic rational Bezier stored as a centre c (float) plus offsets of
+// the control points from c, so that near queries lose no precision to the
+// absolute magnitude of the coordinates:
+//   (o0 o1) (o2 o3) (w0 w1 w2 w3) (c.x c.y 0 0)
+constexpr int kLeaf2Vec = 4;
+constexpr int kLeaf2F64 = 12;  // absolute (x0 y0 x1 y1 x2 y2 x3 y3 w0 w1 w2 w3)
+
+// 3D leaf: local [0,1]^2 rational bicubic Bezier net (16 homogeneous points),
+// box, mean normal, and ranges into the boundary-curve tables.
+constexpr int kNet3Vec = 16;   // float4 (w x, w y, w z, w) per leaf
+struct Leaf3Info {
+    float lo[3], hi[3];        // control-net box
+    float nrm[3];              // unit mean normal (string direction for near queries)
+    float diag;                // box diagonal
+    int32_t c3_off, c3_cnt;    // 3D boundary curves (composition of trims with the surface)
+    int32_t c2_off, c2_cnt;    // 2D boundary curves in local (u, v) for the trim membership test
+};
+
+// A 3D boundary curve: rational Bezier of degree deg (<= kMaxC3Deg) stored as
+// deg + 1 homogeneous points starting at ctrl_off in the curve-point array,
+// counted `mult` times (winding multiplicity of a clipped rectangle edge).
+constexpr int kMaxC3Deg = 18;
+struct Curve3Info {
+    int32_t ctrl_off;
+    int32_t deg;
+    float mult;
+    float pad;
+};
+
+// 2D boundary curve in local (u, v): rational cubic, 4 homogeneous points.
+constexpr int kC2Vec = 3;      // float4 per 2D local curve: (h0 h1 h2 h3) as 12 floats, multiplicity kept in Curve2Mult
+
+struct DevTree {
+    int dim;
+    int n_leaves;
+    int n_internal;
+    int root;                  // 0, or ~0 when the model has a single leaf
+    // internal nodes
+    const float4* hdr;         // (x0.x, x0.y, x0.z, r^2)
+    const int2* child;
+    const float4* mom;         // kMom2Vec or kMom3Vec per node
+    const double* hdr64;       // 4 per node
+    const double* mom64;       // kMom2F64 or kMom3F64 per node
+    // 2D leaves
+    const float4* leaf2;       // kLeaf2Vec per leaf
+    const double* leaf2_64;    // kLeaf2F64 per leaf
+    // 3D leaves
+    const Leaf3Info* leaf3;
+    const float4* net3;        // kNet3Vec per leaf
+    const double* net3_64;     // 64 per leaf
+    const Curve3Info* c3;
+    const float4* c3pts;
+    const double* c3pts64;     // 4 per point
+    const float4* c2;          // kC2Vec per local curve
+    const double* c2_64;       // 12 per local curve
+    const float* c2mult;
+};
+
+struct QueryParams {
+    float beta2;               // beta^2 of the FP32 pass
+    double beta2_repair;       // beta^2 of the FP64 repair pass; <= 0: direct sum
+    float band;                // repair band around half-integers
+    int mode;                  // GWN_MODE_*
+    int precision;             // GWN_PREC_*
+};
+
+}  // namespace gwn

@@ -1,0 +1,112 @@
+"""CPU-side checks of libgwn.so: exported ABI, host-side build (Algorithm 1
+preprocessing) against the oracle's plain moment integrals, and input
+validation.  No GPU is used: models are built with GWN_DEVICE_HOST_ONLY."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2605_19200_gb300 as gwn
+from synth import configs
+from synth import geometry as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HOST_ONLY = -2
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "gwn.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(gwn_[a-z0-9_]+)\s*\(", hdr))
+    assert len(names) >= 10
+    lib = ctypes.CDLL(gwn.native.build())
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def _leaves_under(child, node):
+    out, st = [], [node]
+    while st:
+        k = st.pop()
+        for c in child[k]:
+            if c < 0:
+                out.append(~c)
+            else:
+                st.append(c)
+    return out
+
+
+def test_tree_is_a_valid_binary_radix_tree():
+    curves, _ = configs.loops_2d(n_loops=20, per_loop=30, res=8)
+    m = gwn.gwn_build_2d(curves, device=HOST_ONLY)
+    info = m.info()
+    tr = m.tree()
+    n = info["n_leaves"]
+    assert info["n_nodes"] == n - 1
+    leaves = _leaves_under(tr["child"], 0)
+    assert sorted(leaves) == list(range(n))
+    internal = [c for pair in tr["child"] for c in pair if c >= 0]
+    assert sorted(internal) == list(range(1, n - 1))
+
+
+def test_subdivision_respects_the_box_threshold(oracle_lib):
+    curves = [G.circle((0, 0), 1.0), G.arc((0.3, 0.1), 0.2, 0.0, 1.0)]
+    m = gwn.gwn_build_2d(curves, device=HOST_ONLY, max_aabb_frac=0.1)
+    prim, param = m.leaves()
+    lo, hi = G.shape_bbox_2d(curves)
+    lim = 0.1 * np.linalg.norm(hi - lo)
+    for c in range(len(curves)):
+        sel = np.nonzero(prim == c)[0]
+        iv = param[sel, :2]
+        iv = iv[np.argsort(iv[:, 0])]
+        assert iv[0, 0] == curves[c].knots[0] and iv[-1, 1] == curves[c].knots[-1]
+        np.testing.assert_array_equal(iv[1:, 0], iv[:-1, 1])      # contiguous cover
+    # each leaf's curve lies in a box below the threshold (sampled from the oracle's evaluator)
+    for i in range(len(prim)):
+        t = np.linspace(param[i, 0], param[i, 1], 50)
+        P = oracle_lib.curve_eval(curves[prim[i]], t)
+        assert np.linalg.norm(P.max(0) - P.min(0)) < lim
+
+
+def test_node_moments_match_plain_integrals(oracle_lib):
+    """Up-swept, centred moments (Section 3.1) equal the oracle's quadrature of
+    the chords of the node's leaves about the node centroid."""
+    curves, _ = configs.star_2d(n_queries=4)
+    m = gwn.gwn_build_2d(curves, device=HOST_ONLY)
+    prim, param = m.leaves()
+    tr = m.tree()
+    chords = np.zeros((len(prim), 4))
+    for i in range(len(prim)):
+        P = oracle_lib.curve_eval(curves[prim[i]], param[i, :2])
+        chords[i] = [P[0, 0], P[0, 1], P[1, 0], P[1, 1]]
+    for node in [0, 1, 5, 17, len(prim) - 2]:
+        L = _leaves_under(tr["child"], node)
+        ref = oracle_lib.segment_moments(chords[L], tr["x0"][node])
+        got = tr["mom"][node]
+        np.testing.assert_allclose(got[:2], ref["m0"], atol=1e-12)
+        np.testing.assert_allclose(got[2:6], ref["m1"].ravel(), atol=1e-12)
+        np.testing.assert_allclose(got[6:14], ref["m2"].ravel(), atol=1e-12)
+        # centroid = chord-length-weighted centroid, radius = half box diagonal
+        lens = np.linalg.norm(chords[L, 2:] - chords[L, :2], axis=1)
+        mids = 0.5 * (chords[L, :2] + chords[L, 2:])
+        np.testing.assert_allclose(tr["x0"][node], (lens[:, None] * mids).sum(0) / lens.sum(), atol=1e-12)
+
+
+@pytest.mark.parametrize("bad,code", [
+    (G.Curve(4, np.zeros((5, 2)), np.ones(5), G.bezier_knots(4)), "INVALID_ARG"),
+    (G.Curve(2, np.zeros((4, 2)), np.ones(4), np.array([0, 0.1, 0.2, 0.3, 0.7, 0.8, 1.0])), "INVALID_GEOMETRY"),
+    (G.Curve(1, np.zeros((2, 2)), np.array([1.0, -1.0]), G.bezier_knots(1)), "INVALID_GEOMETRY"),
+    (G.Curve(1, np.array([[0, 0], [np.nan, 1]]), np.ones(2), G.bezier_knots(1)), "INVALID_GEOMETRY"),
+])
+def test_invalid_input_rejected(bad, code):
+    with pytest.raises(gwn.GwnError, match=code):
+        gwn.gwn_build_2d([bad], device=HOST_ONLY)
+
+
+def test_invalid_options_rejected():
+    curves = [G.circle()]
+    for kw in ({"beta": 1.5}, {"order": 3}, {"repair_band": 0.7}, {"beta_repair": 1.0}):
+        with pytest.raises(gwn.GwnError, match="INVALID_ARG"):
+            gwn.gwn_build_2d(curves, device=HOST_ONLY, **kw)

@@ -102,13 +102,17 @@ typedef struct {
     double max_aabb_frac; /* subdivide until a leaf's box diagonal < frac * shape diagonal (0.1); <= 0: no subdivision */
     int32_t order;        /* Taylor order 0, 1 or 2 (default 2) */
     double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2 (default 2) */
-    double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves (default 0) */
+    double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves;
+                             < 0 = automatic: direct sum up to 4096 leaves, else 4 x beta (default -1) */
     double repair_band;   /* re-evaluate in FP64 when |w - round(w) +- 1/2| < band (default 1e-3) */
     int32_t quad_nodes;   /* Gauss-Legendre nodes per rule for 3D moments (default 10) */
     int32_t precision;    /* GWN_PREC_* (default GWN_PREC_FP32_REPAIR) */
     int32_t device;       /* CUDA device ordinal, -1 = current (default -1); GWN_DEVICE_HOST_ONLY
                              builds the host-side tree only (inspection, no queries) */
     int32_t n_threads;    /* host threads for the build, 0 = all (default 0) */
+    int32_t leaf_far;     /* 1: a leaf that passes the far test is approximated by its own moments
+                             (only leaves containing the query are evaluated exactly); 0: every
+                             leaf reached is evaluated exactly; -1: 1 in 3D, 0 in 2D (default) */
 } gwn_build_opts;
 
 /* Fills *opts with the defaults listed above. */

@@ -208,6 +208,40 @@ static void fold_moments_3d(const double* m, int order, double* f) {
     }
 }
 
+// Centroid (weighted, or the box centre when the weight is zero), radius (half
+// the box diagonal) and the moments centred at the centroid: the moment
+// transform of Section 3.1,
+//   int (x - x0) n         = int x n - x0 (x) int n
+//   int (x - x0)(x - x0) n = int x x n - x0 (x) int x n - (int x n with x0 in the
+//                            second slot) + x0 (x) x0 (x) int n,
+// with the uncentred moments m taken about the reference point xref.
+static void centre_block(int d, const double* box, double w, const double* wx, const double* m, const double* xref,
+                         double* x0, double* radius, double* c) {
+    double rr = 0;
+    for (int k = 0; k < d; ++k) {
+        double e = box[d + k] - box[k];
+        rr += e * e;
+        x0[k] = w > 0 ? wx[k] / w : 0.5 * (box[k] + box[d + k]);
+    }
+    *radius = 0.5 * std::sqrt(rr);
+    double y[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) y[k] = x0[k] - xref[k];
+    const double* m0 = m;
+    const double* m1 = m + d;
+    const double* m2 = m + d + d * d;
+    double* c0 = c;
+    double* c1 = c + d;
+    double* c2 = c + d + d * d;
+    for (int k = 0; k < d; ++k) c0[k] = m0[k];
+    for (int i = 0; i < d; ++i)
+        for (int k = 0; k < d; ++k) c1[i * d + k] = m1[i * d + k] - y[i] * m0[k];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+            for (int k = 0; k < d; ++k)
+                c2[(i * d + j) * d + k] =
+                    m2[(i * d + j) * d + k] - y[i] * m1[j * d + k] - y[j] * m1[i * d + k] + y[i] * y[j] * m0[k];
+}
+
 void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm) {
     const int d = L.dim;
     const int n = (int)L.wsum.size();
@@ -331,6 +365,31 @@ void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* p
     }
     (void)leaf_box;
 
+    // far-field data of every leaf (moments centred at the leaf's own centroid)
+    {
+        const int fv = d == 2 ? kMom2Vec : kMom3Vec;
+        const int ff = d == 2 ? kMom2F64 : kMom3F64;
+        out->lhdr.assign(n, float4{0, 0, 0, 0});
+        out->lhdr64.assign((size_t)n * 4, 0.0);
+        out->lmom.assign((size_t)n * fv, float4{0, 0, 0, 0});
+        out->lmom64.assign((size_t)n * ff, 0.0);
+        std::vector<double> c(M);
+        for (int i = 0; i < n; ++i) {
+            int li = (*perm)[i];
+            double x0[3] = {0, 0, 0}, radius;
+            centre_block(d, &L.box[(size_t)li * 2 * d], L.wsum[li], &L.wx[(size_t)li * d], &L.mom[(size_t)li * M],
+                         L.xref, x0, &radius, c.data());
+            double f[kMom3F64];
+            if (d == 2) fold_moments_2d(c.data(), order, f); else fold_moments_3d(c.data(), order, f);
+            for (int k = 0; k < ff; ++k) out->lmom64[(size_t)i * ff + k] = f[k];
+            float* fp = reinterpret_cast<float*>(&out->lmom[(size_t)i * fv]);
+            for (int k = 0; k < 4 * fv; ++k) fp[k] = k < ff ? (float)f[k] : 0.0f;
+            out->lhdr[i] = float4{(float)x0[0], (float)x0[1], (float)x0[2], (float)(radius * radius)};
+            for (int k = 0; k < 3; ++k) out->lhdr64[i * 4 + k] = x0[k];
+            out->lhdr64[i * 4 + 3] = radius * radius;
+        }
+    }
+
     // centre in place and pack
     out->x0.assign((size_t)ni * d, 0.0);
     out->r.assign(ni, 0.0);
@@ -342,33 +401,9 @@ void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* p
     out->mom.assign((size_t)ni * fv, float4{0, 0, 0, 0});
     out->mom64.assign((size_t)ni * ff, 0.0);
     for (int node = 0; node < ni; ++node) {
-        const double* bx = &nbox[node * 2 * d];
-        double x0[3] = {0, 0, 0}, rr = 0;
-        for (int k = 0; k < d; ++k) {
-            double e = bx[d + k] - bx[k];
-            rr += e * e;
-            x0[k] = nw[node] > 0 ? nwx[node * d + k] / nw[node] : 0.5 * (bx[k] + bx[d + k]);
-        }
-        double radius = 0.5 * std::sqrt(rr);
-        // centring about x0 (relative to the moments' reference point)
-        double y[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) y[k] = x0[k] - L.xref[k];
-        const double* m = &nmom[(size_t)node * M];
-        const double* m0 = m;
-        const double* m1 = m + d;
-        const double* m2 = m + d + d * d;
+        double x0[3] = {0, 0, 0}, radius;
         double* c = &out->mom_c[(size_t)node * M];
-        double* c0 = c;
-        double* c1 = c + d;
-        double* c2 = c + d + d * d;
-        for (int k = 0; k < d; ++k) c0[k] = m0[k];
-        for (int i = 0; i < d; ++i)
-            for (int k = 0; k < d; ++k) c1[i * d + k] = m1[i * d + k] - y[i] * m0[k];
-        for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j)
-                for (int k = 0; k < d; ++k)
-                    c2[(i * d + j) * d + k] = m2[(i * d + j) * d + k] - y[i] * m1[j * d + k] - y[j] * m1[i * d + k] +
-                                              y[i] * y[j] * m0[k];
+        centre_block(d, &nbox[node * 2 * d], nw[node], &nwx[node * d], &nmom[(size_t)node * M], L.xref, x0, &radius, c);
         for (int k = 0; k < d; ++k) out->x0[node * d + k] = x0[k];
         out->r[node] = radius;
         double f[kMom3F64];

@@ -24,6 +24,11 @@ struct HostModel {
     std::vector<float4> mom;
     std::vector<double> hdr64;
     std::vector<double> mom64;
+    // per-leaf far-field data (BVH order), used when leaves take the far test
+    std::vector<float4> lhdr;
+    std::vector<float4> lmom;
+    std::vector<double> lhdr64;
+    std::vector<double> lmom64;
     std::vector<double> x0;        // dim per node, absolute coordinates
     std::vector<double> r;         // radius per node
     std::vector<double> mom_c;     // centred moments per node (d + d^2 + d^3)

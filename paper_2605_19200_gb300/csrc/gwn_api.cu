@@ -61,6 +61,7 @@ struct DeviceGuard {
 
 struct gwn_model_s {
     int dim = 2;
+    int leaf_far = 0;
     int device = 0;
     int64_t n_primitives = 0;
     gwn_build_opts opts{};
@@ -106,7 +107,55 @@ void free_model_memory(gwn_model_s* m) {
     m->stage = nullptr;
 }
 
+// constant tables of the 3D kernels (binomial coefficients, 8-point
+// Gauss-Legendre rule on [0, 1]); uploaded once per device
+std::mutex g_const_mu;
+bool g_const_ready[256];
+
+gwn_status init_constants(int dev) {
+    std::lock_guard<std::mutex> lk(g_const_mu);
+    if (dev < 0 || dev >= 256) return fail(GWN_ERR_INVALID_ARG, "device ordinal out of range");
+    if (g_const_ready[dev]) return GWN_OK;
+    float bin[kMaxC3Deg + 1][kMaxC3Deg + 1] = {};
+    for (int a = 0; a <= kMaxC3Deg; ++a) {
+        bin[a][0] = bin[a][a] = 1.f;
+        for (int b = 1; b < a; ++b) bin[a][b] = bin[a - 1][b - 1] + bin[a - 1][b];
+    }
+    double x[8], w[8];
+    for (int i = 0; i < 8; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / 8.5), pp = 1;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1, p2 = 0;
+            for (int j = 1; j <= 8; ++j) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = 8 * (z * p1 - p2) / (z * z - 1);
+            double dz = p1 / pp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1 - z);
+        w[i] = 1.0 / ((1 - z * z) * pp * pp);
+    }
+    std::memcpy(h_binom, bin, sizeof(bin));
+    std::memcpy(h_glx8, x, sizeof(x));
+    std::memcpy(h_glw8, w, sizeof(w));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx8, x, sizeof(x)));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw8, w, sizeof(w)));
+    g_const_ready[dev] = true;
+    return GWN_OK;
+}
+
 gwn_status upload_model(gwn_model_s* m) {
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        gwn_status cs = init_constants(dev);
+        if (cs != GWN_OK) return cs;
+    }
     const HostModel& H = m->host;
     DevTree& t = m->tree;
     t.dim = H.dim;
@@ -115,6 +164,11 @@ gwn_status upload_model(gwn_model_s* m) {
     t.root = H.n_leaves > 1 ? 0 : ~0;
     gwn_status s;
 #define UP(vec, field) if ((s = upload(m, H.vec, &t.field)) != GWN_OK) return s
+    t.leaf_far = m->leaf_far;
+    UP(lhdr, lhdr);
+    UP(lmom, lmom);
+    UP(lhdr64, lhdr64);
+    UP(lmom64, lmom64);
     UP(hdr, hdr);
     UP(child, child);
     UP(mom, mom);
@@ -149,7 +203,7 @@ gwn_status finish_build(gwn_model_s* m, gwn_model* out) {
 gwn_status check_opts(const gwn_build_opts& o) {
     if (!(o.beta >= 2.0) || !std::isfinite(o.beta)) return fail(GWN_ERR_INVALID_ARG, "beta must be >= 2");
     if (o.order < 0 || o.order > 2) return fail(GWN_ERR_INVALID_ARG, "order must be 0, 1 or 2");
-    if (!(o.beta_repair == 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be 0 or >= 2");
+    if (!(o.beta_repair <= 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be <= 0 or >= 2");
     if (!(o.repair_band >= 0.0 && o.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
     if (o.quad_nodes < 1 || o.quad_nodes > 32) return fail(GWN_ERR_INVALID_ARG, "quad_nodes must be 1..32");
     if (o.precision < 0 || o.precision > 2) return fail(GWN_ERR_INVALID_ARG, "unknown precision");
@@ -315,7 +369,9 @@ gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t
     QueryParams p;
     double beta = qo.beta > 0 ? qo.beta : m->opts.beta;
     p.beta2 = (float)(beta * beta);
-    p.beta2_repair = m->opts.beta_repair > 0 ? m->opts.beta_repair * m->opts.beta_repair : 0.0;
+    double br = m->opts.beta_repair;
+    if (br < 0) br = m->host.n_leaves <= 4096 ? 0.0 : 4.0 * beta;  // automatic choice
+    p.beta2_repair = br > 0 ? br * br : 0.0;
     p.band = (float)m->opts.repair_band;
     p.mode = qo.mode;
     p.precision = qo.precision >= 0 ? qo.precision : m->opts.precision;
@@ -354,12 +410,13 @@ void gwn_default_build_opts(gwn_build_opts* o) {
     o->max_aabb_frac = 0.1;
     o->order = 2;
     o->beta = 2.0;
-    o->beta_repair = 0.0;
+    o->beta_repair = -1.0;
     o->repair_band = 1e-3;
     o->quad_nodes = 10;
     o->precision = GWN_PREC_FP32_REPAIR;
     o->device = -1;
     o->n_threads = 0;
+    o->leaf_far = -1;
 }
 
 void gwn_default_query_opts(gwn_query_opts* q) {
@@ -382,6 +439,7 @@ static gwn_status build_common(int dim, const void* prims, size_t n, const gwn_b
     if (!m) return fail(GWN_ERR_OOM, "host allocation failed");
     m->dim = dim;
     m->opts = o;
+    m->leaf_far = o.leaf_far < 0 ? (dim == 3 ? 1 : 0) : (o.leaf_far ? 1 : 0);
     m->n_primitives = (int64_t)n;
     gwn_status code = GWN_OK;
     std::string err;

@@ -24,6 +24,19 @@ struct alignas(16) float4 { float x, y, z, w; };
 struct alignas(8) int2 { int x, y; };
 #endif
 
+// Device routines are also compiled for the host (GWN_HD) so that they can be
+// exercised on a CPU; GWN_LDG is a read-only cached load on the device.
+#ifdef __CUDACC__
+#define GWN_HD __host__ __device__
+#else
+#define GWN_HD
+#endif
+#if defined(__CUDA_ARCH__)
+#define GWN_LDG(p) __ldg(p)
+#else
+#define GWN_LDG(p) (*(p))
+#endif
+
 namespace gwn {
 
 constexpr int kMom2Vec = 3;    // float4 per 2D moment block (12 floats)
@@ -41,7 +54,8 @@ constexpr int kLeaf2F64 = 12;  // absolute (x0 y0 x1 y1 x2 y2 x3 y3 w0 w1 w2 w3)
 // box, mean normal, and ranges into the boundary-curve tables.
 constexpr int kNet3Vec = 16;   // float4 (w x, w y, w z, w) per leaf
 struct Leaf3Info {
-    float lo[3], hi[3];        // control-net box
+    float cen[3];              // leaf centre; float geometry of the leaf is stored relative to it
+    float rad;                 // half the box diagonal
     float nrm[3];              // unit mean normal (string direction for near queries)
     float diag;                // box diagonal
     int32_t c3_off, c3_cnt;    // 3D boundary curves (composition of trims with the surface)
@@ -67,6 +81,12 @@ struct DevTree {
     int n_leaves;
     int n_internal;
     int root;                  // 0, or ~0 when the model has a single leaf
+    int leaf_far;              // 1: leaves also take the far test (their own moments)
+    // per-leaf far-field data (same layout as the nodes)
+    const float4* lhdr;
+    const float4* lmom;
+    const double* lhdr64;
+    const double* lmom64;
     // internal nodes
     const float4* hdr;         // (x0.x, x0.y, x0.z, r^2)
     const int2* child;

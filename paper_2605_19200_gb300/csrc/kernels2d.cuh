@@ -27,21 +27,30 @@ constexpr int kStack64 = 96;
 
 template <typename T> struct Num;
 template <> struct Num<float> {
-    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
-    static __device__ __forceinline__ float inv_(float x) { return __frcp_rn(x); }
-    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    static GWN_HD inline float atan2_(float y, float x) { return atan2f(y, x); }
+#if defined(__CUDA_ARCH__)
+    static GWN_HD inline float inv_(float x) { return __frcp_rn(x); }
+    static GWN_HD inline float rsqrt_(float x) { return rsqrtf(x); }
+#else
+    static GWN_HD inline float inv_(float x) { return 1.0f / x; }
+    static GWN_HD inline float rsqrt_(float x) { return 1.0f / sqrtf(x); }
+#endif
     static constexpr float inv2pi = 0.15915494309189535f;
 };
 template <> struct Num<double> {
-    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
-    static __device__ __forceinline__ double inv_(double x) { return 1.0 / x; }
-    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static GWN_HD inline double atan2_(double y, double x) { return atan2(y, x); }
+    static GWN_HD inline double inv_(double x) { return 1.0 / x; }
+#if defined(__CUDA_ARCH__)
+    static GWN_HD inline double rsqrt_(double x) { return rsqrt(x); }
+#else
+    static GWN_HD inline double rsqrt_(double x) { return 1.0 / sqrt(x); }
+#endif
     static constexpr double inv2pi = 0.15915494309189533577;
 };
 
 // split a cubic (3 homogeneous components) at t; keep the part selected by `left`
 template <typename T>
-__device__ __forceinline__ void cubic_part(T (&h)[4][3], T t, bool left) {
+GWN_HD inline void cubic_part(T (&h)[4][3], T t, bool left) {
     T a[3], b[3], c[3], d[3], e[3], f[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -65,7 +74,7 @@ __device__ __forceinline__ void cubic_part(T (&h)[4][3], T t, bool left) {
 // points H (coordinates relative to q).  Returns false if more than maxlevel
 // bisection levels would be needed.
 template <typename T>
-__device__ bool curve_angle(const T (&H)[4][3], int maxlevel, T* out) {
+GWN_HD bool curve_angle(const T (&H)[4][3], int maxlevel, T* out) {
     T acc = 0;
     int level = 0;
     unsigned long long idx = 0;
@@ -113,9 +122,9 @@ __device__ bool curve_angle(const T (&H)[4][3], int maxlevel, T* out) {
 }
 
 // GWN of 2D leaf `li` at q; FP32 with the FP64 near band.
-__device__ __forceinline__ float leaf2_eval32(const DevTree& t, int li, float qx, float qy, uint32_t& st) {
+GWN_HD inline float leaf2_eval32(const DevTree& t, int li, float qx, float qy, uint32_t& st) {
     const float4* L = t.leaf2 + (size_t)li * kLeaf2Vec;
-    float4 v0 = __ldg(L + 0), v1 = __ldg(L + 1), v2 = __ldg(L + 2), v3 = __ldg(L + 3);
+    float4 v0 = GWN_LDG(L + 0), v1 = GWN_LDG(L + 1), v2 = GWN_LDG(L + 2), v3 = GWN_LDG(L + 3);
     // q relative to the leaf centre, then control points relative to q
     float rx = qx - v3.x, ry = qy - v3.y;
     float px[4] = {v0.x - rx, v0.z - rx, v1.x - rx, v1.z - rx};
@@ -151,7 +160,7 @@ __device__ __forceinline__ float leaf2_eval32(const DevTree& t, int li, float qx
     return (float)(ad * Num<double>::inv2pi);
 }
 
-__device__ __forceinline__ double leaf2_eval64(const DevTree& t, int li, double qx, double qy, uint32_t& st) {
+GWN_HD inline double leaf2_eval64(const DevTree& t, int li, double qx, double qy, uint32_t& st) {
     const double* D = t.leaf2_64 + (size_t)li * kLeaf2F64;
     double Hd[4][3];
     double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
@@ -174,7 +183,7 @@ __device__ __forceinline__ double leaf2_eval64(const DevTree& t, int li, double 
 }
 
 template <typename T>
-__device__ __forceinline__ T far2_eval(const T* f, T rx, T ry) {
+GWN_HD inline T far2_eval(const T* f, T rx, T ry) {
     T r2 = rx * rx + ry * ry;
     T i2 = Num<T>::inv_(r2);
     T t0 = f[0] * rx + f[1] * ry + f[2];
@@ -184,7 +193,7 @@ __device__ __forceinline__ T far2_eval(const T* f, T rx, T ry) {
 }
 
 // Algorithm 1 for one 2D query, FP32.
-__device__ float query2_32(const DevTree& t, float qx, float qy, float beta2, uint32_t& st) {
+GWN_HD float query2_32(const DevTree& t, float qx, float qy, float beta2, uint32_t& st) {
     float w = 0.f;
     int stack[kStack32];
     int sp = 0;
@@ -193,15 +202,15 @@ __device__ float query2_32(const DevTree& t, float qx, float qy, float beta2, ui
         if (node < 0) {
             w += leaf2_eval32(t, ~node, qx, qy, st);
         } else {
-            float4 h = __ldg(t.hdr + node);
+            float4 h = GWN_LDG(t.hdr + node);
             float rx = h.x - qx, ry = h.y - qy;
             if (rx * rx + ry * ry > beta2 * h.w) {
                 const float4* M = t.mom + (size_t)node * kMom2Vec;
-                float4 a = __ldg(M), b = __ldg(M + 1), c = __ldg(M + 2);
+                float4 a = GWN_LDG(M), b = GWN_LDG(M + 1), c = GWN_LDG(M + 2);
                 float f[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
                 w += far2_eval<float>(f, rx, ry);
             } else {
-                int2 ch = __ldg(t.child + node);
+                int2 ch = GWN_LDG(t.child + node);
                 if (sp < kStack32) stack[sp++] = ch.y; else st |= GWN_QS_STACK_OVERFLOW;
                 node = ch.x;
                 continue;
@@ -214,7 +223,7 @@ __device__ float query2_32(const DevTree& t, float qx, float qy, float beta2, ui
 }
 
 // Algorithm 1 in FP64 (repair pass); beta2 <= 0 evaluates every leaf directly.
-__device__ double query2_64(const DevTree& t, double qx, double qy, double beta2, uint32_t& st) {
+GWN_HD double query2_64(const DevTree& t, double qx, double qy, double beta2, uint32_t& st) {
     double w = 0.0;
     if (beta2 <= 0.0) {
         for (int i = 0; i < t.n_leaves; ++i) w += leaf2_eval64(t, i, qx, qy, st);

@@ -1,30 +1,511 @@
 // kernels3d.cuh -- device routines of the 3D query (Algorithm 1, query half).
+//
+// leaf3_eval: exact GWN of one trimmed leaf (Section 3.3) by a Stokes
+//   reduction of Eq. 2.  With a unit vector s, the potential
+//       A_s(r) = (s x r) / (|r| (|r| + s . r))
+//   satisfies curl A_s = r / |r|^3 off the half line {q - t s, t > 0}, so
+//       w = (1/4pi) sum_c mult_c int A_s(x_c(t) - q) . x_c'(t) dt  -  sum_hits wind sign(s . n)
+//   where x_c are the leaf's boundary curves (trims composed with the surface,
+//   built by build3d.cpp) and the hits are crossings of the half line with the
+//   visible surface.
+//   * q outside the sphere around the leaf's box (radius 1.1 x half diagonal):
+//     s points from q to the box centre.  The half line then leaves the box
+//     behind (no hits), and every boundary point is seen at more than 90 degrees
+//     from the half line, so the integrand is smooth.
+//   * otherwise s is the leaf's mean normal, oriented so that the half line
+//     points away from the leaf's mid-plane.  The leaf is a graph along its mean
+//     normal (normal cone below 55 degrees, enforced by the build), so the half
+//     line meets it at most once: the foot point is found by Newton's method on
+//     the two tangential components, and counted if it lies on the half line
+//     and inside the leaf's visible region (winding number of its local 2D
+//     boundary).
+//   The line integral uses 8-point Gauss-Legendre panels, bisected (stackless,
+//   by level and index) until each panel is shorter than PanelRatio times its
+//   distance to q.  FP32 stops at kLevel32 bisections; a leaf that needs more, or
+//   whose foot point is too close to call in FP32, is evaluated again in FP64:
+//   the near-boundary band.
+// far3: the order-2 Taylor expansion of Eq. 3 in folded form (gwn_internal.h).
 #pragma once
 
 #include "gwn_internal.h"
+#include "kernels2d.cuh"
 #include "../../include/gwn.h"
 
 namespace gwn {
 
-__device__ __forceinline__ float leaf3_eval32(const DevTree& t, int li, float qx, float qy, float qz, uint32_t& st) {
-    (void)t; (void)li; (void)qx; (void)qy; (void)qz;
-    st |= GWN_QS_UNRESOLVED;
-    return 0.f;
+constexpr int kLevel32 = 10;
+constexpr int kLevel64 = 40;
+// panel length / distance-to-q bound of the 8-point rule: the quadrature error
+// of an analytic integrand decays like rho^-16 with rho the Bernstein-ellipse
+// parameter, ~3.0 at 1.5 (FP32, ~1e-8 relative) and ~6.7 at 0.6 (FP64, ~1e-13)
+template <typename T> struct PanelRatio;
+template <> struct PanelRatio<float> { static constexpr float v = 1.5f; };
+template <> struct PanelRatio<double> { static constexpr double v = 0.6; };
+
+// binomial coefficients and the 8-point Gauss-Legendre rule on [0, 1]: device
+// constant memory, with host mirrors for host-side execution
+__constant__ float c_binom[kMaxC3Deg + 1][kMaxC3Deg + 1];
+__constant__ double c_glx8[8];
+__constant__ double c_glw8[8];
+static float h_binom[kMaxC3Deg + 1][kMaxC3Deg + 1];
+static double h_glx8[8], h_glw8[8];
+#if defined(__CUDA_ARCH__)
+#define GWN_BINOM(d, i) c_binom[d][i]
+#define GWN_GLX(k) c_glx8[k]
+#define GWN_GLW(k) c_glw8[k]
+#else
+#define GWN_BINOM(d, i) h_binom[d][i]
+#define GWN_GLX(k) h_glx8[k]
+#define GWN_GLW(k) h_glw8[k]
+#endif
+
+// accessors of one leaf's geometry, in FP32 (relative to the leaf centre) or FP64 (absolute)
+struct Geo32 {
+    const float4* net;
+    const float4* pts;
+    GWN_HD inline void net_pt(int k, float h[4]) const {
+        float4 v = GWN_LDG(net + k);
+        h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+    }
+    GWN_HD inline void pt(int k, float h[4]) const {
+        float4 v = GWN_LDG(pts + k);
+        h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+    }
+};
+struct Geo64 {
+    const double* net;
+    const double* pts;
+    GWN_HD inline void net_pt(int k, double h[4]) const {
+        for (int c = 0; c < 4; ++c) h[c] = net[k * 4 + c];
+    }
+    GWN_HD inline void pt(int k, double h[4]) const {
+        for (int c = 0; c < 4; ++c) h[c] = pts[k * 4 + c];
+    }
+};
+
+// value and derivative (homogeneous) of a degree-D Bernstein curve by Horner's rule
+template <typename T, typename G>
+GWN_HD inline void bern4(const G& g, int D, T t, T X[4], T dX[4]) {
+    const bool rev = t > T(0.5);
+    const T a = rev ? T(1) - t : t;
+    const T b = T(1) - a;
+    const T r = a / b;
+    T acc[4] = {0, 0, 0, 0}, dacc[4] = {0, 0, 0, 0};
+    T hi[4], lo[4];
+    // value: sum_i C(D,i) c_i a^i b^(D-i), walked from i = D down to 0
+    g.pt(rev ? 0 : D, hi);
+    for (int c = 0; c < 4; ++c) acc[c] = hi[c];
+    for (int i = D - 1; i >= 0; --i) {
+        g.pt(rev ? D - i : i, lo);
+        T cb = (T)GWN_BINOM(D, i);
+        T cd = (T)GWN_BINOM(D - 1, i);
+        for (int c = 0; c < 4; ++c) {
+            dacc[c] = (i == D - 1) ? (hi[c] - lo[c]) : dacc[c] * r + cd * (hi[c] - lo[c]);
+            acc[c] = acc[c] * r + cb * lo[c];
+            hi[c] = lo[c];
+        }
+    }
+    // scale by b^D and b^(D-1)
+    T pw = T(1), base = b;
+    int e = D - 1;
+    while (e > 0) {
+        if (e & 1) pw *= base;
+        base *= base;
+        e >>= 1;
+    }
+    T sgn = rev ? T(-1) : T(1);
+    for (int c = 0; c < 4; ++c) {
+        X[c] = acc[c] * pw * b;
+        dX[c] = sgn * T(D) * dacc[c] * pw;
+    }
 }
-__device__ __forceinline__ double leaf3_eval64(const DevTree& t, int li, double qx, double qy, double qz, uint32_t& st) {
-    (void)t; (void)li; (void)qx; (void)qy; (void)qz;
-    st |= GWN_QS_UNRESOLVED;
-    return 0.0;
+
+template <typename T> struct Gl8;
+template <> struct Gl8<float> {
+    static GWN_HD inline float x(int k) { return (float)GWN_GLX(k); }
+    static GWN_HD inline float w(int k) { return (float)GWN_GLW(k); }
+};
+template <> struct Gl8<double> {
+    static GWN_HD inline double x(int k) { return GWN_GLX(k); }
+    static GWN_HD inline double w(int k) { return GWN_GLW(k); }
+};
+
+// int A_s(x(t) - q) . x'(t) dt over one boundary curve, adaptive; sets deep if
+// the panel limit was hit
+template <typename T, typename G>
+GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int maxlevel, bool& deep) {
+    T acc = 0;
+    int level = 0;
+    unsigned long long idx = 0;
+    while (true) {
+        const T h = T(1) / T(1ull << level);
+        const T a = T(idx) * h;
+        T psum = 0, dmin2 = T(1e30), len = 0;
+        T px = 0, py = 0, pz = 0;
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            T X[4], dX[4];
+            bern4<T>(g, D, a + h * Gl8<T>::x(k), X, dX);
+            T iw = T(1) / X[3];
+            T x0 = X[0] * iw, x1 = X[1] * iw, x2 = X[2] * iw;
+            T d0 = (dX[0] - x0 * dX[3]) * iw, d1 = (dX[1] - x1 * dX[3]) * iw, d2 = (dX[2] - x2 * dX[3]) * iw;
+            T r0 = x0 - q[0], r1 = x1 - q[1], r2 = x2 - q[2];
+            T rr = r0 * r0 + r1 * r1 + r2 * r2;
+            T rn = sqrt(rr);
+            T sr = s[0] * r0 + s[1] * r1 + s[2] * r2;
+            T c0 = s[1] * r2 - s[2] * r1, c1 = s[2] * r0 - s[0] * r2, c2 = s[0] * r1 - s[1] * r0;
+            T f = (c0 * d0 + c1 * d1 + c2 * d2) / (rn * (rn + sr));
+            psum += Gl8<T>::w(k) * f;
+            dmin2 = fmin(dmin2, rr);
+            if (k > 0) {
+                T e0 = x0 - px, e1 = x1 - py, e2 = x2 - pz;
+                len += sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+            }
+            px = x0; py = x1; pz = x2;
+        }
+        // the 8 nodes span ~96% of the panel
+        len *= T(1.1);
+        bool refine = len * len > T(PanelRatio<T>::v * PanelRatio<T>::v) * dmin2;
+        if (refine && level < maxlevel) {
+            ++level;
+            idx <<= 1;
+            continue;
+        }
+        if (refine) deep = true;
+        acc += psum * h;
+        while (idx & 1ull) {
+            idx >>= 1;
+            --level;
+        }
+        if (level == 0) break;
+        ++idx;
+    }
+    return acc;
 }
-__device__ __forceinline__ float query3_32(const DevTree& t, float qx, float qy, float qz, float beta2, uint32_t& st) {
-    (void)t; (void)qx; (void)qy; (void)qz; (void)beta2;
-    st |= GWN_QS_UNRESOLVED;
-    return 0.f;
+
+// S, S_u, S_v of the leaf's bicubic net at local (u, v)
+template <typename T, typename G>
+GWN_HD void net_eval3(const G& g, T u, T v, T S[3], T Su[3], T Sv[3]) {
+    T su = T(1) - u, sv = T(1) - v;
+    T Bu[4] = {su * su * su, T(3) * u * su * su, T(3) * u * u * su, u * u * u};
+    T Bv[4] = {sv * sv * sv, T(3) * v * sv * sv, T(3) * v * v * sv, v * v * v};
+    T dBu[4] = {T(-3) * su * su, T(3) * su * su - T(6) * u * su, T(6) * u * su - T(3) * u * u, T(3) * u * u};
+    T dBv[4] = {T(-3) * sv * sv, T(3) * sv * sv - T(6) * v * sv, T(6) * v * sv - T(3) * v * v, T(3) * v * v};
+    T H[4] = {0, 0, 0, 0}, Hu[4] = {0, 0, 0, 0}, Hv[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            T h[4];
+            g.net_pt(i * 4 + j, h);
+            T b = Bu[i] * Bv[j], bu = dBu[i] * Bv[j], bv = Bu[i] * dBv[j];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                H[c] += b * h[c];
+                Hu[c] += bu * h[c];
+                Hv[c] += bv * h[c];
+            }
+        }
+    T iw = T(1) / H[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        S[c] = H[c] * iw;
+        Su[c] = (Hu[c] - S[c] * Hu[3]) * iw;
+        Sv[c] = (Hv[c] - S[c] * Hv[3]) * iw;
+    }
 }
-__device__ __forceinline__ double query3_64(const DevTree& t, double qx, double qy, double qz, double beta2, uint32_t& st) {
-    (void)t; (void)qx; (void)qy; (void)qz; (void)beta2;
-    st |= GWN_QS_UNRESOLVED;
-    return 0.0;
+
+enum { kHitNone = 0, kHitOk = 1, kHitUnsure = 2 };
+
+// winding number of the leaf's local 2D boundary around (u, v); returns false if
+// (u, v) is too close to the boundary to decide at this precision
+template <typename T>
+GWN_HD bool local_winding(const DevTree& t, const Leaf3Info& I, T u, T v, int maxlevel, int* wind) {
+    T acc = 0;
+    for (int c = 0; c < I.c2_cnt; ++c) {
+        T H[4][3];
+        int k = I.c2_off + c;
+        if (sizeof(T) == 4) {
+            const float4* C = t.c2 + (size_t)k * kC2Vec;
+            float4 a = GWN_LDG(C), b = GWN_LDG(C + 1), d = GWN_LDG(C + 2);
+            float f[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
+            for (int i = 0; i < 4; ++i) {
+                H[i][0] = (T)f[3 * i] - u * (T)f[3 * i + 2];
+                H[i][1] = (T)f[3 * i + 1] - v * (T)f[3 * i + 2];
+                H[i][2] = (T)f[3 * i + 2];
+            }
+        } else {
+            const double* C = t.c2_64 + (size_t)k * 12;
+            for (int i = 0; i < 4; ++i) {
+                H[i][0] = (T)C[3 * i] - u * (T)C[3 * i + 2];
+                H[i][1] = (T)C[3 * i + 1] - v * (T)C[3 * i + 2];
+                H[i][2] = (T)C[3 * i + 2];
+            }
+        }
+        T a;
+        if (!curve_angle<T>(H, maxlevel, &a)) return false;
+        acc += (T)t.c2mult[k] * a;
+    }
+    *wind = (int)round(acc * Num<T>::inv2pi);
+    return true;
+}
+
+// crossing of the half line {q + tau sig n, tau > 0} with the leaf: *contrib =
+// wind * sign(s . N) with s = -sig n, to be subtracted from the line integral
+template <typename T, typename G>
+GWN_HD int leaf_hit(const DevTree& t, const Leaf3Info& I, const G& g, const T q[3], const T nrm[3], T sig, T diag,
+                        T* contrib, int maxlevel) {
+    *contrib = 0;
+    // tangent basis
+    T e1[3], e2[3];
+    {
+        T ax = fabs(nrm[0]) < T(0.9) ? T(1) : T(0), ay = T(1) - ax;
+        // e1 = normalize(a x n) with a = x or y axis
+        T a[3] = {ax, ay, 0};
+        e1[0] = a[1] * nrm[2] - a[2] * nrm[1];
+        e1[1] = a[2] * nrm[0] - a[0] * nrm[2];
+        e1[2] = a[0] * nrm[1] - a[1] * nrm[0];
+        T l = Num<T>::rsqrt_(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        e1[0] *= l; e1[1] *= l; e1[2] *= l;
+        e2[0] = nrm[1] * e1[2] - nrm[2] * e1[1];
+        e2[1] = nrm[2] * e1[0] - nrm[0] * e1[2];
+        e2[2] = nrm[0] * e1[1] - nrm[1] * e1[0];
+    }
+    // quick reject: q's projection outside the projected control-net box
+    T mn1 = T(1e30), mx1 = T(-1e30), mn2 = T(1e30), mx2 = T(-1e30);
+    for (int k = 0; k < 16; ++k) {
+        T h[4];
+        g.net_pt(k, h);
+        T iw = T(1) / h[3];
+        T p1 = (h[0] * iw - q[0]) * e1[0] + (h[1] * iw - q[1]) * e1[1] + (h[2] * iw - q[2]) * e1[2];
+        T p2 = (h[0] * iw - q[0]) * e2[0] + (h[1] * iw - q[1]) * e2[1] + (h[2] * iw - q[2]) * e2[2];
+        mn1 = fmin(mn1, p1); mx1 = fmax(mx1, p1);
+        mn2 = fmin(mn2, p2); mx2 = fmax(mx2, p2);
+    }
+    if (mn1 > 0 || mx1 < 0 || mn2 > 0 || mx2 < 0) return kHitNone;
+    // exact test: winding number of the projected domain boundary (the net's
+    // four edge curves, rational cubics) around q's projection.  Zero means the
+    // line along the normal misses the leaf's rectangle altogether.
+    {
+        T acc = 0;
+        for (int e = 0; e < 4; ++e) {
+            T H[4][3];
+            for (int k = 0; k < 4; ++k) {
+                // bottom (v=0, u up), right (u=1, v up), top (v=1, u down), left (u=0, v down)
+                int i = e == 0 ? k : (e == 1 ? 3 : (e == 2 ? 3 - k : 0));
+                int j = e == 0 ? 0 : (e == 1 ? k : (e == 2 ? 3 : 3 - k));
+                T h[4];
+                g.net_pt(i * 4 + j, h);
+                T dx = h[0] - q[0] * h[3], dy = h[1] - q[1] * h[3], dz = h[2] - q[2] * h[3];
+                H[k][0] = e1[0] * dx + e1[1] * dy + e1[2] * dz;
+                H[k][1] = e2[0] * dx + e2[1] * dy + e2[2] * dz;
+                H[k][2] = h[3];
+            }
+            T a;
+            if (!curve_angle<T>(H, maxlevel, &a)) return kHitUnsure;  // q over the rectangle's edge
+            acc += a;
+        }
+        if (fabs(acc) < T(3.14159265)) return kHitNone;  // winding number 0
+    }
+    T u = T(0.5), v = T(0.5);
+    bool conv = false;
+    T S[3], Su[3], Sv[3];
+    const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
+    for (int it = 0; it < 40; ++it) {
+        net_eval3<T>(g, u, v, S, Su, Sv);
+        T d[3] = {S[0] - q[0], S[1] - q[1], S[2] - q[2]};
+        T F1 = e1[0] * d[0] + e1[1] * d[1] + e1[2] * d[2];
+        T F2 = e2[0] * d[0] + e2[1] * d[1] + e2[2] * d[2];
+        T J00 = e1[0] * Su[0] + e1[1] * Su[1] + e1[2] * Su[2];
+        T J01 = e1[0] * Sv[0] + e1[1] * Sv[1] + e1[2] * Sv[2];
+        T J10 = e2[0] * Su[0] + e2[1] * Su[1] + e2[2] * Su[2];
+        T J11 = e2[0] * Sv[0] + e2[1] * Sv[1] + e2[2] * Sv[2];
+        T det = J00 * J11 - J01 * J10;
+        if (!(fabs(det) > T(0))) break;
+        T du = (J11 * F1 - J01 * F2) / det, dv = (J00 * F2 - J10 * F1) / det;
+        u -= du;
+        v -= dv;
+        u = fmin(fmax(u, T(-0.5)), T(1.5));
+        v = fmin(fmax(v, T(-0.5)), T(1.5));
+        if (fabs(du) + fabs(dv) < tol) {
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) return kHitUnsure;
+    const T eps = sizeof(T) == 4 ? T(1e-5) : T(1e-12);
+    if (u < -eps || u > T(1) + eps || v < -eps || v > T(1) + eps) return kHitNone;
+    net_eval3<T>(g, u, v, S, Su, Sv);
+    T tau = sig * (nrm[0] * (S[0] - q[0]) + nrm[1] * (S[1] - q[1]) + nrm[2] * (S[2] - q[2]));
+    T tau_eps = sizeof(T) == 4 ? T(1e-4) * diag : T(1e-12) * diag;
+    if (fabs(tau) < tau_eps) return kHitUnsure;  // q too close to the surface to decide here
+    if (u < eps || u > T(1) - eps || v < eps || v > T(1) - eps) return kHitUnsure;  // on the leaf's rectangle edge
+    if (tau < 0) return kHitNone;
+    int wind = 0;
+    if (!local_winding<T>(t, I, u, v, maxlevel, &wind)) return kHitUnsure;
+    if (wind == 0) return kHitNone;
+    T N[3] = {Su[1] * Sv[2] - Su[2] * Sv[1], Su[2] * Sv[0] - Su[0] * Sv[2], Su[0] * Sv[1] - Su[1] * Sv[0]};
+    // s = -sig nrm; the crossing enters the Stokes identity as wind * sign(s . N)
+    T sn = -sig * (nrm[0] * N[0] + nrm[1] * N[1] + nrm[2] * N[2]);
+    *contrib = (T)wind * (sn > 0 ? T(1) : T(-1));
+    return kHitOk;
+}
+
+// GWN of leaf li at q (q relative to the leaf geometry's origin); false if the
+// precision of T could not resolve it
+template <typename T, typename G>
+GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T q[3], T* out, int maxlevel) {
+    T nrm[3] = {(T)I.nrm[0], (T)I.nrm[1], (T)I.nrm[2]};
+    T cen[3];
+    if (sizeof(T) == 4) {
+        cen[0] = cen[1] = cen[2] = T(0);
+    } else {
+        cen[0] = (T)I.cen[0]; cen[1] = (T)I.cen[1]; cen[2] = (T)I.cen[2];
+    }
+    T dq[3] = {q[0] - cen[0], q[1] - cen[1], q[2] - cen[2]};
+    T d2 = dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2];
+    T rfar = T(1.1) * (T)I.rad;
+    T s[3];
+    T hits = 0;
+    if (d2 > rfar * rfar) {
+        T l = Num<T>::rsqrt_(d2);
+        s[0] = -dq[0] * l; s[1] = -dq[1] * l; s[2] = -dq[2] * l;
+    } else {
+        T sig = (dq[0] * nrm[0] + dq[1] * nrm[1] + dq[2] * nrm[2]) >= 0 ? T(1) : T(-1);
+        s[0] = -sig * nrm[0]; s[1] = -sig * nrm[1]; s[2] = -sig * nrm[2];
+        int hr = leaf_hit<T>(t, I, g, q, nrm, sig, (T)I.diag, &hits, sizeof(T) == 4 ? kNear32 : kMaxLevel64);
+        if (hr == kHitUnsure) return false;
+    }
+    T acc = 0;
+    bool deep = false;
+    for (int c = 0; c < I.c3_cnt; ++c) {
+        Curve3Info ci = t.c3[I.c3_off + c];
+        G gc = g;
+        if (sizeof(T) == 4) gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts + ci.ctrl_off);
+        else gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts64 + (size_t)ci.ctrl_off * 4);
+        acc += (T)ci.mult * curve_line_integral<T>(gc, ci.deg, q, s, maxlevel, deep);
+    }
+    if (deep) return false;
+    *out = acc * T(0.07957747154594767) - hits;  // 1 / (4 pi)
+    return true;
+}
+
+GWN_HD inline double leaf3_eval64(const DevTree& t, int li, double qx, double qy, double qz, uint32_t& st) {
+    Leaf3Info I = t.leaf3[li];
+    Geo64 g{t.net3_64 + (size_t)li * 64, nullptr};
+    double q[3] = {qx, qy, qz};
+    double w = 0;
+    if (!leaf3_core<double>(t, I, g, q, &w, kLevel64)) st |= GWN_QS_UNRESOLVED;
+    return w;
+}
+
+GWN_HD inline float leaf3_eval32(const DevTree& t, int li, float qx, float qy, float qz, uint32_t& st) {
+    Leaf3Info I = t.leaf3[li];
+    Geo32 g{t.net3 + (size_t)li * kNet3Vec, nullptr};
+    float q[3] = {qx - I.cen[0], qy - I.cen[1], qz - I.cen[2]};
+    float w = 0;
+    if (leaf3_core<float>(t, I, g, q, &w, kLevel32)) return w;
+    st |= GWN_QS_NEAR;
+    return (float)leaf3_eval64(t, li, (double)qx, (double)qy, (double)qz, st);
+}
+
+template <typename T>
+GWN_HD inline T far3_eval(const T* f, T rx, T ry, T rz) {
+    T r2 = rx * rx + ry * ry + rz * rz;
+    T i2 = T(1) / r2;
+    T i3 = i2 * Num<T>::rsqrt_(r2);
+    T t0 = f[0] * rx + f[1] * ry + f[2] * rz + f[3];
+    T xx = rx * rx, yy = ry * ry, zz = rz * rz;
+    T t1 = f[4] * xx + f[5] * yy + f[6] * zz + f[7] * rx * ry + f[8] * rx * rz + f[9] * ry * rz + f[10] * rx + f[11] * ry +
+           f[12] * rz;
+    T t2 = rx * (f[13] * xx + f[16] * rx * ry + f[17] * rx * rz + f[18] * yy + f[20] * zz + f[22] * ry * rz) +
+           ry * (f[14] * yy + f[19] * ry * rz + f[21] * zz) + f[15] * zz * rz;
+    return i3 * (t0 + i2 * (t1 + i2 * t2));
+}
+
+GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz) {
+    float4 a = GWN_LDG(M), b = GWN_LDG(M + 1), c = GWN_LDG(M + 2), d = GWN_LDG(M + 3), e = GWN_LDG(M + 4), f4 = GWN_LDG(M + 5);
+    float f[24] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w,
+                   d.x, d.y, d.z, d.w, e.x, e.y, e.z, e.w, f4.x, f4.y, f4.z, f4.w};
+    return far3_eval<float>(f, rx, ry, rz);
+}
+
+// Algorithm 1 for one 3D query, FP32
+GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float beta2, uint32_t& st) {
+    float w = 0.f;
+    int stack[kStack32];
+    int sp = 0;
+    int node = t.root;
+    while (true) {
+        if (node < 0) {
+            int li = ~node;
+            bool done = false;
+            if (t.leaf_far) {
+                float4 h = GWN_LDG(t.lhdr + li);
+                float rx = h.x - qx, ry = h.y - qy, rz = h.z - qz;
+                if (rx * rx + ry * ry + rz * rz > beta2 * h.w) {
+                    w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
+                    done = true;
+                }
+            }
+            if (!done) w += leaf3_eval32(t, li, qx, qy, qz, st);
+        } else {
+            float4 h = GWN_LDG(t.hdr + node);
+            float rx = h.x - qx, ry = h.y - qy, rz = h.z - qz;
+            if (rx * rx + ry * ry + rz * rz > beta2 * h.w) {
+                w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz);
+            } else {
+                int2 ch = GWN_LDG(t.child + node);
+                if (sp < kStack32) stack[sp++] = ch.y; else st |= GWN_QS_STACK_OVERFLOW;
+                node = ch.x;
+                continue;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return w;
+}
+
+// Algorithm 1 in FP64 (repair pass); beta2 <= 0 evaluates every leaf directly
+GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, double beta2, uint32_t& st) {
+    double w = 0.0;
+    if (beta2 <= 0.0) {
+        for (int i = 0; i < t.n_leaves; ++i) w += leaf3_eval64(t, i, qx, qy, qz, st);
+        return w;
+    }
+    int stack[kStack64];
+    int sp = 0;
+    int node = t.root;
+    while (true) {
+        if (node < 0) {
+            int li = ~node;
+            bool done = false;
+            if (t.leaf_far) {
+                const double* h = t.lhdr64 + (size_t)li * 4;
+                double rx = h[0] - qx, ry = h[1] - qy, rz = h[2] - qz;
+                if (rx * rx + ry * ry + rz * rz > beta2 * h[3]) {
+                    w += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
+                    done = true;
+                }
+            }
+            if (!done) w += leaf3_eval64(t, li, qx, qy, qz, st);
+        } else {
+            const double* h = t.hdr64 + (size_t)node * 4;
+            double rx = h[0] - qx, ry = h[1] - qy, rz = h[2] - qz;
+            if (rx * rx + ry * ry + rz * rz > beta2 * h[3]) {
+                w += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz);
+            } else {
+                int2 ch = t.child[node];
+                if (sp < kStack64) stack[sp++] = ch.y; else st |= GWN_QS_UNRESOLVED;
+                node = ch.x;
+                continue;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return w;
 }
 
 }  // namespace gwn

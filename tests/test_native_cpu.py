@@ -110,3 +110,53 @@ def test_invalid_options_rejected():
     for kw in ({"beta": 1.5}, {"order": 3}, {"repair_band": 0.7}, {"beta_repair": 1.0}):
         with pytest.raises(gwn.GwnError, match="INVALID_ARG"):
             gwn.gwn_build_2d(curves, device=HOST_ONLY, **kw)
+
+
+def test_3d_root_moments_match_plain_integrals(oracle_lib):
+    """Leaves cut by the subdivision (trims clipped to the leaf rectangles),
+    Green's-theorem quadrature per leaf and the up-sweep: the root's centred
+    moments equal the oracle's fan cubature of every patch about the root
+    centroid."""
+    patches, _ = configs.sphere_3d(n_queries=4)
+    m = gwn.gwn_build_3d(patches, device=HOST_ONLY)
+    prim, param = m.leaves()
+    assert len(prim) > len(patches)          # some patches were subdivided
+    tr = m.tree()
+    x0 = tr["x0"][0]
+    tot = {k: 0 for k in ("m0", "m1", "m2")}
+    area = 0.0
+    for p in patches:
+        r = oracle_lib.patch_moments(p, x0, nsub=2)
+        for k in tot:
+            tot[k] = tot[k] + r[k]
+        area += r["area"]
+    got = tr["mom"][0]
+    scale = area
+    np.testing.assert_allclose(got[:3], tot["m0"], atol=1e-10 * scale)
+    np.testing.assert_allclose(got[3:12], tot["m1"].ravel(), atol=1e-10 * scale)
+    np.testing.assert_allclose(got[12:39], tot["m2"].ravel(), atol=1e-10 * scale)
+
+
+def test_3d_leaf_moments_additive_over_subdivision(oracle_lib):
+    """A trimmed patch split into many leaves: the subtree of its leaves carries
+    the patch's moments (checked on a single-patch model)."""
+    patches, _ = configs.sphere_3d(n_queries=4)
+    p = patches[7]
+    m = gwn.gwn_build_3d([p], device=HOST_ONLY, max_aabb_frac=0.2)
+    prim, param = m.leaves()
+    assert len(prim) >= 4
+    tr = m.tree()
+    ref = oracle_lib.patch_moments(p, tr["x0"][0], nsub=2)
+    np.testing.assert_allclose(tr["mom"][0][:3], ref["m0"], atol=1e-12)
+    np.testing.assert_allclose(tr["mom"][0][3:12], ref["m1"].ravel(), atol=1e-12)
+    np.testing.assert_allclose(tr["mom"][0][12:39], ref["m2"].ravel(), atol=1e-12)
+
+
+def test_3d_invalid_input_rejected():
+    good = G.planar_patch((0, 0, 0), (1, 0, 0), (0, 1, 0))
+    bad_trim = G.planar_patch((0, 0, 0), (1, 0, 0), (0, 1, 0), trims=[G.circle((0.9, 0.5), 0.3)])
+    with pytest.raises(gwn.GwnError, match="INVALID_GEOMETRY"):
+        gwn.gwn_build_3d([good, bad_trim], device=HOST_ONLY)
+    bad_w = G.Patch(1, 1, good.ctrl, -good.weights, good.knots_u, good.knots_v, [])
+    with pytest.raises(gwn.GwnError, match="INVALID_GEOMETRY"):
+        gwn.gwn_build_3d([bad_w], device=HOST_ONLY)

@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the batched GWN containment query on one GB300.
+
+Workload (default): 16 models of trimmed bicubic rational patches (overlapping
+perturbed box/cylinder unions, 1k-40k patches each, weights U[0.8, 1.2], an
+outer polygonal trim loop and 0-2 polygonal holes per patch), queries
+log-uniform in [65,536, 4,194,304] per model, uniform in each model's box --
+the synthetic stand-in for the paper's CAD collection (Section 4.4).  One
+step queries every model once (FP32 bulk with FP64 repair, beta chosen to meet
+max |dGWN| <= 1e-4).  value = queries/s with points already on the device;
+e2e = the same through the C ABI with pinned host buffers, copies included.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl gwn|reference]
+
+Multi-GPU: the query is data-parallel with no exchange step; N ranks run N
+independent replicas of the whole step ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+T_START = time.time()
+
+
+def log(msg):
+    print(f"[bench {time.time() - T_START:7.1f}s] {msg}", file=sys.stderr, flush=True)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+BETA = 0.0              # 0: the build's autotuner picks beta and beta_leaf per model for max |dGWN| <= 1e-4
+DIRECT_SAMPLE = 40960   # queries per model for the plain direct-sum comparison (fills the GPU)
+ORACLE_SAMPLE = 2       # queries per model for the CPU oracle
+
+
+def build_workload(scale_queries: float = 1.0, n_models: int = 16):
+    from synth import configs
+    return configs.cad_batch_3d(query_scale=scale_queries)[:n_models]
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flops_traversal(w):
+    # per internal node / leaf visited: far test (10); per Taylor evaluation: 72
+    return 10 * (w["nodes"] + w["leaf_tests"]) + 72 * w["far"]
+
+
+def flops_leaves(w):
+    # per Gauss-Legendre node of a degree-D boundary curve: 28 D + 70 (value and
+    # derivative by Horner's rule, string potential); per foot-point search 2000;
+    # per leaf evaluation set-up 30
+    return 28 * w["gl_deg"] + 70 * w["gl_nodes"] + 2000 * w["hits"] + 30 * w["leaves"]
+
+
+def fp32_peak_tflops(sm_mhz, sms):
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_oracle_sample(workload, per_model, threads):
+    import oracle
+    t0 = time.perf_counter()
+    nq = 0
+    for patches, q in workload:
+        oracle.gwn3d(patches, q[:per_model], n_threads=threads)
+        nq += min(per_model, q.shape[0])
+    return nq, time.perf_counter() - t0
+
+
+def reference_arm(args):
+    """The oracle (plain FP64 CPU direct sum) timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    workload = build_workload()
+    threads = os.cpu_count() or 1
+    per = 1
+    for _ in range(args.warmup):
+        run_oracle_sample(workload, per, threads)
+    tot_q, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        nq, dt = run_oracle_sample(workload, per, threads)
+        tot_q += nq
+        tot_t += dt
+    val = tot_q / tot_t
+    sample = f"{per} query per model x 16 models per step (exact FP64 direct sum over every patch)"
+    line = {"metric": "GWN queries/s (batched containment, 16 trimmed-NURBS models)", "value": val,
+            "unit": "queries/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cad16: 16 models, 1k-40k trimmed bicubic rational patches, 64k-4M queries each",
+                       "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gwn", choices=["gwn", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--models", type=int, default=16, help="first K models of the workload (default all 16)")
+    ap.add_argument("--query-scale", type=float, default=1.0, help="fraction of each model's queries (default 1)")
+    ap.add_argument("--beta", type=float, default=BETA)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="timed steps only (no e2e, direct-sum or CPU legs); for profiler runs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2605_19200_gb300 as gwn
+
+    t0 = time.perf_counter()
+    workload = build_workload(args.query_scale, args.models)
+    log("workload generated")
+    models, points, outs = [], [], []
+    for patches, q in workload:
+        m = gwn.gwn_build_3d(patches, beta=args.beta)
+        models.append(m)
+        pt = torch.from_numpy(q.astype(np.float32)).to(dev)
+        points.append(pt)
+        n = pt.shape[0]
+        outs.append((torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+                     torch.empty(n, dtype=torch.int32, device=dev)))
+    setup_s = time.perf_counter() - t0
+    log(f"built {len(models)} models; (beta, beta_leaf) per model: "
+        f"{[(round(m.info()['beta'], 1), round(m.info()['beta_leaf'], 1)) for m in models]}")
+    total_q = sum(p.shape[0] for p in points)
+    tuned = [(round(m.info()["beta"], 2), round(m.info()["beta_leaf"], 2)) for m in models]
+    n_leaves = sum(m.info()["n_leaves"] for m in models)
+    n_patches = sum(len(p) for p, _ in workload)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for m, p, o in zip(models, points, outs):
+            m.query(p, out=o, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        torch.cuda.synchronize()
+        log("warm-up step")
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clk.stop()
+    log(f"timed {args.steps} steps: {ms:.1f} ms/step")
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * total_q / (ms / 1e3)
+
+    if args.kernels_only:
+        if rank == 0:
+            print(json.dumps({"metric": "GWN queries/s (kernels-only run)", "value": value, "unit": "queries/s",
+                              "ms_per_step": ms, "queries_per_step": total_q}), flush=True)
+        return
+
+    # kernel-level numbers (untimed passes): event timing of the traversal and
+    # exact-leaf kernels on the query stream, and the algorithmic work counters
+    trav_us, leaf_us, fl_trav, fl_leaf, repaired, pairs = 0.0, 0.0, 0.0, 0.0, 0, 0
+    for m, p, o in zip(models, points, outs):
+        m.query(p, out=o, stream=stream, profile=True)
+        s = m.last_query_stats()
+        trav_us += s["trav_us"]
+        leaf_us += s["leaf_us"]
+        m.query(p, out=o, stream=stream, count_work=True)
+        w = m.last_query_stats()
+        fl_trav += flops_traversal(w)
+        fl_leaf += flops_leaves(w)
+        repaired += w["repaired"]
+        pairs += w["pairs"]
+    log("profiled and counted")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = fp32_peak_tflops(sm_mhz, sms)
+    dominant = "k_pair_eval" if leaf_us >= trav_us else "k_trav3"
+    d_us, d_fl = (leaf_us, fl_leaf) if dominant == "k_pair_eval" else (trav_us, fl_trav)
+    # per launch: algorithmic flops / event-timed duration (summed over the 16 launches of a step)
+    achieved = d_fl / (d_us * 1e-6) / 1e12
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": f"FP32 FMA issue: {sms} SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median under load)",
+                "trav_ms_per_step": trav_us / 1e3, "leaf_ms_per_step": leaf_us / 1e3}
+
+    # e2e through the C ABI with pinned host buffers (copies in the timed region)
+    host_pts = [p.cpu().pin_memory() for p in points]
+    host_out = [(torch.empty(p.shape[0], dtype=torch.float64).pin_memory(),
+                 torch.empty(p.shape[0], dtype=torch.int32).pin_memory(), None) for p in points]
+
+    def step_e2e():
+        for m, hp, ho in zip(models, host_pts, host_out):
+            gwn.gwn_query(m, hp, out=ho, want_status=False, stream=stream)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t1) / e2e_steps
+    log(f"e2e {e2e_s * 1e3:.1f} ms/step")
+    h2d = sum(p.numel() * 4 for p in points)
+    d2h = sum(p.shape[0] * (8 + 4) for p in points)
+
+    # plain GPU direct sum on a sample of each model's queries (unsubdivided patches)
+    direct_q, direct_ms = 0, 0.0
+    for (patches, q), p in zip(workload, points):
+        md = gwn.gwn_build_3d(patches, max_aabb_frac=0.0)
+        sub = p[:DIRECT_SAMPLE].contiguous()
+        md.query(sub, mode=gwn.MODE_DIRECT, stream=stream)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        md.query(sub, mode=gwn.MODE_DIRECT, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        # per-query cost is independent of the batch size: extrapolate to the model's queries
+        direct_ms += a.elapsed_time(b) * (p.shape[0] / sub.shape[0])
+        direct_q += p.shape[0]
+        del md
+    direct_qps = direct_q / (direct_ms / 1e3)
+    log(f"direct sum {direct_qps:.3e} q/s")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        nq, dt = run_oracle_sample(workload, ORACLE_SAMPLE, threads)
+        cpu = {"value": nq / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
+               "sample": f"{ORACLE_SAMPLE} queries of each of the 16 models (exact FP64 direct sum), {dt:.1f} s"}
+
+    # kernels per chunk of up to 2^19 points: bin, scan, scatter; 3 rounds of traversal, pair key, scan,
+    # pair scatter, pair eval, near band (+ round switch x2); overflow, finish, repair x3, counter accumulate
+    launches_per_step = sum(29 * math.ceil(p.shape[0] / (1 << 19)) for p in points)
+    line = {
+        "metric": "GWN queries/s (batched containment, 16 trimmed-NURBS models)",
+        "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cad16: 16 models of trimmed bicubic rational patches (box/cylinder unions), "
+                               "queries uniform in each model's box",
+                   "models": len(models), "patches": n_patches, "leaves": n_leaves, "queries_per_step": total_q,
+                   "beta": "autotuned" if args.beta == 0 else args.beta, "beta_per_model": tuned,
+                   "tolerance": 1e-4, "order": 2, "precision": "fp32 bulk + fp64 repair",
+                   "l2": f"inputs larger than L2 ({total_q * 12 / 1e6:.0f} MB of points per step)",
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1)},
+        "e2e": {"value": world * total_q / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roofline,
+        "direct_sum": {"value": direct_qps, "unit": "queries/s",
+                       "sample": f"{DIRECT_SAMPLE} queries per model, FP32, per-query time extrapolated",
+                       "speedup": value / direct_qps},
+        "work": {"pairs_per_query": pairs / total_q, "repaired_fraction": repaired / total_q},
+        "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -101,9 +101,10 @@ typedef struct {
     double tolerance;     /* target max |dGWN| for the FP32 path (default 1e-4) */
     double max_aabb_frac; /* subdivide until a leaf's box diagonal < frac * shape diagonal (0.1); <= 0: no subdivision */
     int32_t order;        /* Taylor order 0, 1 or 2 (default 2) */
-    double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2 (default 2) */
+    double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2, or 0 = choose
+                             beta (and beta_leaf) by the autotuner to meet `tolerance` (default 2) */
     double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves;
-                             < 0 = automatic: direct sum up to 4096 leaves, else 4 x beta (default -1) */
+                             < 0 = automatic: direct sum up to 4096 leaves, else 2 x beta (default -1) */
     double repair_band;   /* re-evaluate in FP64 when |w - round(w) +- 1/2| < band (default 1e-3) */
     int32_t quad_nodes;   /* Gauss-Legendre nodes per rule for 3D moments (default 10) */
     int32_t precision;    /* GWN_PREC_* (default GWN_PREC_FP32_REPAIR) */
@@ -113,15 +114,19 @@ typedef struct {
     int32_t leaf_far;     /* 1: a leaf that passes the far test is approximated by its own moments
                              (only leaves containing the query are evaluated exactly); 0: every
                              leaf reached is evaluated exactly; -1: 1 in 3D, 0 in 2D (default) */
+    double beta_leaf;     /* far-test factor of the leaves themselves when leaf_far is on; 0 = beta (default 0) */
 } gwn_build_opts;
 
 /* Fills *opts with the defaults listed above. */
 void gwn_default_build_opts(gwn_build_opts* opts);
 
 typedef struct {
-    int32_t mode;      /* GWN_MODE_* (default GWN_MODE_BVH) */
-    int32_t precision; /* GWN_PREC_*, or -1 = the model's (default -1) */
-    double beta;       /* 0 = the model's */
+    int32_t mode;       /* GWN_MODE_* (default GWN_MODE_BVH) */
+    int32_t precision;  /* GWN_PREC_*, or -1 = the model's (default -1) */
+    double beta;        /* 0 = the model's */
+    int32_t count_work; /* 1: count algorithmic work units (slower; see gwn_last_query_stats) */
+    int32_t profile;    /* 1: time the traversal and exact-leaf kernels with CUDA events on the stream */
+    double beta_leaf;   /* 0 = the model's */
 } gwn_query_opts;
 
 void gwn_default_query_opts(gwn_query_opts* opts);
@@ -165,9 +170,23 @@ typedef struct {
     double beta, beta_repair, repair_band;
     int32_t order;
     double lo[3], hi[3];    /* box of all control points */
+    double beta_leaf;       /* far-test factor of the leaves (3D; equals beta unless set or tuned) */
 } gwn_model_stats;
 
 gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
+
+/* Work counters of the last gwn_query on this model (synchronises the
+ * device).  out holds 16 int64:
+ *   out[0] exact-leaf (point, leaf) pairs of the 3D traversal
+ *   out[1] points re-evaluated in FP64 (repair)
+ *   out[2] 3D leaf evaluations moved to the FP64 near band
+ *   out[3] points whose pairs did not fit the work list
+ *   out[4..11] with count_work: internal nodes visited, leaves visited, Taylor
+ *     evaluations, exact leaf evaluations, Gauss-Legendre nodes, sum of curve
+ *     degrees over those nodes, foot-point searches, (reserved)
+ *   out[12..13] with profile: traversal and exact-leaf kernel time in
+ *     microseconds (CUDA events on the query's stream) */
+gwn_status gwn_last_query_stats(gwn_model model, int64_t* out);
 
 /* Copy per-leaf records to host memory for inspection (used by the tests).
  * For each leaf i in BVH order: prim[i] = input primitive index and

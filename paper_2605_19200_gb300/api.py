@@ -48,11 +48,12 @@ class gwn_build_opts(ctypes.Structure):
     _fields_ = [("tolerance", ctypes.c_double), ("max_aabb_frac", ctypes.c_double), ("order", ctypes.c_int32),
                 ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double), ("repair_band", ctypes.c_double),
                 ("quad_nodes", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("n_threads", ctypes.c_int32), ("leaf_far", ctypes.c_int32)]
+                ("n_threads", ctypes.c_int32), ("leaf_far", ctypes.c_int32), ("beta_leaf", ctypes.c_double)]
 
 
 class gwn_query_opts(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double)]
+    _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("count_work", ctypes.c_int32), ("profile", ctypes.c_int32), ("beta_leaf", ctypes.c_double)]
 
 
 class gwn_model_stats(ctypes.Structure):
@@ -60,7 +61,7 @@ class gwn_model_stats(ctypes.Structure):
                 ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("build_ms", ctypes.c_double), ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double),
                 ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3)]
+                ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -72,6 +73,7 @@ _SIGS = {
     "gwn_query": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t, _P, _P, _P,
                                  ctypes.POINTER(gwn_query_opts), _P]),
     "gwn_model_info": (ctypes.c_int, [_P, ctypes.POINTER(gwn_model_stats)]),
+    "gwn_last_query_stats": (ctypes.c_int, [_P, _P]),
     "gwn_model_leaves": (ctypes.c_int, [_P, _P, _P]),
     "gwn_model_tree": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gwn_release": (ctypes.c_int, [_P]),
@@ -176,6 +178,13 @@ class Model:
         _check(lib().gwn_model_info(self.handle, ctypes.byref(s)))
         return {f: (list(getattr(s, f)) if f in ("lo", "hi") else getattr(s, f)) for f, _ in s._fields_}
 
+    def last_query_stats(self) -> dict:
+        out = np.zeros(16, dtype=np.int64)
+        _check(lib().gwn_last_query_stats(self.handle, out.ctypes.data))
+        names = ["pairs", "repaired", "near_band", "overflow", "nodes", "leaf_tests", "far", "leaves",
+                 "gl_nodes", "gl_deg", "hits", "chords", "trav_us", "leaf_us"]
+        return {k: int(out[i]) for i, k in enumerate(names)}
+
     def leaves(self):
         n = self.info()["n_leaves"]
         prim = np.zeros(n, dtype=np.int64)
@@ -195,9 +204,11 @@ class Model:
         return {"child": child[:ni], "x0": x0[:ni], "r": r[:ni], "mom": mom[:ni]}
 
     def query(self, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
-              want_label: bool = True, want_status: bool = True):
+              want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
+              out=None, beta_leaf: float = 0.0):
         return gwn_query(self, points, mode=mode, precision=precision, beta=beta, stream=stream,
-                         want_label=want_label, want_status=want_status)
+                         want_label=want_label, want_status=want_status, count_work=count_work, profile=profile,
+                         out=out, beta_leaf=beta_leaf)
 
 
 def gwn_build_2d(curves: Sequence, opts: Optional[gwn_build_opts] = None, **kw) -> Model:
@@ -253,11 +264,14 @@ def _stream_handle(stream):
 
 
 def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
-              want_label: bool = True, want_status: bool = True):
+              want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
+              out=None, beta_leaf: float = 0.0):
     """GWN at points.  torch CUDA tensor -> asynchronous device call with device
     outputs; numpy array or CPU tensor -> host call (staged, synchronous).
-    Returns (w float64, label int32 or None, status uint32/int32 or None)."""
-    q = default_query_opts(mode=mode, precision=precision, beta=beta)
+    Returns (w float64, label int32 or None, status uint32/int32 or None).
+    `out` may supply preallocated outputs (w, label or None, status or None)."""
+    q = default_query_opts(mode=mode, precision=precision, beta=beta, count_work=int(count_work),
+                           profile=int(profile), beta_leaf=beta_leaf)
     try:
         import torch
     except Exception:  # pragma: no cover
@@ -268,9 +282,12 @@ def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, b
             pts = pts.float()
         n = pts.shape[0]
         dt = F32 if pts.dtype == torch.float32 else F64
-        w = torch.empty(n, dtype=torch.float64, device=pts.device)
-        lab = torch.empty(n, dtype=torch.int32, device=pts.device) if want_label else None
-        st = torch.empty(n, dtype=torch.int32, device=pts.device) if want_status else None
+        if out is not None:
+            w, lab, st = out
+        else:
+            w = torch.empty(n, dtype=torch.float64, device=pts.device)
+            lab = torch.empty(n, dtype=torch.int32, device=pts.device) if want_label else None
+            st = torch.empty(n, dtype=torch.int32, device=pts.device) if want_status else None
         _check(lib().gwn_query(model.handle, pts.data_ptr(), dt, MEM_DEVICE, n, w.data_ptr(),
                                lab.data_ptr() if lab is not None else None,
                                st.data_ptr() if st is not None else None, ctypes.byref(q),
@@ -279,17 +296,25 @@ def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, b
     if torch is not None and isinstance(points, torch.Tensor):
         points = points.numpy()
     pts = np.ascontiguousarray(points)
+
+    def _addr(a):
+        if a is None:
+            return None
+        if torch is not None and isinstance(a, torch.Tensor):
+            return a.data_ptr()
+        return a.ctypes.data
     if pts.dtype not in (np.float32, np.float64):
         pts = pts.astype(np.float64)
     n = pts.shape[0]
     dt = F32 if pts.dtype == np.float32 else F64
-    w = np.zeros(n)
-    lab = np.zeros(n, dtype=np.int32) if want_label else None
-    st = np.zeros(n, dtype=np.uint32) if want_status else None
-    _check(lib().gwn_query(model.handle, pts.ctypes.data, dt, MEM_HOST, n, w.ctypes.data,
-                           lab.ctypes.data if lab is not None else None,
-                           st.ctypes.data if st is not None else None, ctypes.byref(q),
-                           _stream_handle(stream)))
+    if out is not None:
+        w, lab, st = out
+    else:
+        w = np.zeros(n)
+        lab = np.zeros(n, dtype=np.int32) if want_label else None
+        st = np.zeros(n, dtype=np.uint32) if want_status else None
+    _check(lib().gwn_query(model.handle, pts.ctypes.data, dt, MEM_HOST, n, _addr(w), _addr(lab), _addr(st),
+                           ctypes.byref(q), _stream_handle(stream)))
     return w, lab, st
 
 

@@ -823,11 +823,25 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
             ci.mult = (float)L.mult[b];
             ci.pad = 0.f;
             out->c3.push_back(ci);
+            // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i);
+            // float copies relative to the leaf centre, double copies absolute
+            std::vector<double> rel((size_t)(D + 1) * 4);
             for (int t = 0; t <= D; ++t) {
                 const double* h = &X[(size_t)t * 4];
-                out->c3pts.push_back(float4{(float)(h[0] - cen[0] * h[3]), (float)(h[1] - cen[1] * h[3]),
-                                            (float)(h[2] - cen[2] * h[3]), (float)h[3]});
-                for (int k = 0; k < 4; ++k) out->c3pts64.push_back(h[k]);
+                double r4[4] = {h[0] - cen[0] * h[3], h[1] - cen[1] * h[3], h[2] - cen[2] * h[3], h[3]};
+                for (int k = 0; k < 4; ++k) rel[(size_t)t * 4 + k] = r4[k];
+                double c = binom(D, t);
+                out->c3pts.push_back(float4{(float)(c * r4[0]), (float)(c * r4[1]), (float)(c * r4[2]), (float)(c * r4[3])});
+                for (int k = 0; k < 4; ++k) out->c3pts64.push_back(c * h[k]);
+            }
+            for (int t = 0; t < D; ++t) {
+                double c = binom(D - 1, t);
+                float f[4];
+                for (int k = 0; k < 4; ++k) {
+                    f[k] = (float)(c * (rel[(size_t)(t + 1) * 4 + k] - rel[(size_t)t * 4 + k]));
+                    out->c3pts64.push_back(c * (X[(size_t)(t + 1) * 4 + k] - X[(size_t)t * 4 + k]));
+                }
+                out->c3pts.push_back(float4{f[0], f[1], f[2], f[3]});
             }
             TP e3 = tp_elevate3(L.bnd[b]);
             float f[12];

@@ -15,6 +15,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -26,6 +28,7 @@
 #include "gwn_internal.h"
 #include "kernels2d.cuh"
 #include "kernels3d.cuh"
+#include "query_pipeline.cuh"
 
 using namespace gwn;
 
@@ -70,11 +73,16 @@ struct gwn_model_s {
     DevTree tree{};
     std::vector<void*> allocs;
     size_t device_bytes = 0;
-    // scratch: repair list + counter, host staging
+    // scratch owned by the model: query workspace and host staging
     std::mutex mu;
-    int* rlist = nullptr;
-    int* rcount = nullptr;
-    size_t rcap = 0;
+    void* ws_mem = nullptr;
+    size_t ws_bytes = 0;
+    size_t ws_n = 0;
+    Workspace ws{};
+    static constexpr int kMaxProfChunks = 32;
+    cudaEvent_t ev[kMaxProfChunks][4] = {};
+    int prof_chunks = 0;
+    bool profiled = false;
     void* stage = nullptr;
     size_t stage_cap = 0;
 };
@@ -99,12 +107,16 @@ gwn_status upload(gwn_model_s* m, const std::vector<V>& v, const V** out) {
 void free_model_memory(gwn_model_s* m) {
     for (void* p : m->allocs) cudaFree(p);
     m->allocs.clear();
-    if (m->rlist) cudaFree(m->rlist);
-    if (m->rcount) cudaFree(m->rcount);
+    if (m->ws_mem) cudaFree(m->ws_mem);
     if (m->stage) cudaFree(m->stage);
-    m->rlist = nullptr;
-    m->rcount = nullptr;
+    for (auto& row : m->ev)
+        for (auto& e : row)
+            if (e) cudaEventDestroy(e), e = nullptr;
+    m->ws_mem = nullptr;
+    m->ws_bytes = 0;
+    m->ws_n = 0;
     m->stage = nullptr;
+    m->stage_cap = 0;
 }
 
 // constant tables of the 3D kernels (binomial coefficients, 8-point
@@ -139,9 +151,18 @@ gwn_status init_constants(int dev) {
         x[i] = 0.5 * (1 - z);
         w[i] = 1.0 / ((1 - z * z) * pp * pp);
     }
+    float xf[8], wf[8];
+    for (int i = 0; i < 8; ++i) {
+        xf[i] = (float)x[i];
+        wf[i] = (float)w[i];
+    }
     std::memcpy(h_binom, bin, sizeof(bin));
     std::memcpy(h_glx8, x, sizeof(x));
     std::memcpy(h_glw8, w, sizeof(w));
+    std::memcpy(h_glx8f, xf, sizeof(xf));
+    std::memcpy(h_glw8f, wf, sizeof(wf));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx8f, xf, sizeof(xf)));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw8f, wf, sizeof(wf)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx8, x, sizeof(x)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw8, w, sizeof(w)));
@@ -201,7 +222,8 @@ gwn_status finish_build(gwn_model_s* m, gwn_model* out) {
 }
 
 gwn_status check_opts(const gwn_build_opts& o) {
-    if (!(o.beta >= 2.0) || !std::isfinite(o.beta)) return fail(GWN_ERR_INVALID_ARG, "beta must be >= 2");
+    if (!(o.beta == 0.0 || o.beta >= 2.0) || !std::isfinite(o.beta)) return fail(GWN_ERR_INVALID_ARG, "beta must be 0 (autotune) or >= 2");
+    if (!(o.beta_leaf == 0.0 || o.beta_leaf >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_leaf must be 0 or >= 2");
     if (o.order < 0 || o.order > 2) return fail(GWN_ERR_INVALID_ARG, "order must be 0, 1 or 2");
     if (!(o.beta_repair <= 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be <= 0 or >= 2");
     if (!(o.repair_band >= 0.0 && o.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
@@ -283,6 +305,12 @@ __global__ void __launch_bounds__(128) k_query64(DevTree t, const void* pts, int
     if (out_status) out_status[i] = st;
 }
 
+__global__ void k_iota(int n, int* list, int* count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) list[i] = i;
+    if (i == 0) *count = n;
+}
+
 // FP64 repair of the listed queries (persistent grid over the device-side
 // count).  With beta_repair > 0 each thread re-runs the traversal in FP64;
 // with beta_repair == 0 (exact direct sum) a whole warp shares one query, its
@@ -331,23 +359,59 @@ __global__ void __launch_bounds__(128) k_repair(DevTree t, const void* pts, int 
         if (lane == 0) {
             out_w[i] = w;
             if (out_label) out_label[i] = (int)round(w);
-            if (out_status) out_status[i] = (out_status[i] | st | GWN_QS_REPAIRED);
+            if (out_status) out_status[i] = (p.precision == GWN_PREC_FP64 ? 0u : out_status[i]) | st | GWN_QS_REPAIRED;
         }
     }
 }
 
-gwn_status ensure_scratch(gwn_model_s* m, size_t n, size_t stage_bytes) {
-    if (n > m->rcap) {
-        if (m->rlist) cudaFree(m->rlist);
-        m->rlist = nullptr;
-        size_t cap = std::max<size_t>(n, 1024);
-        cudaError_t e = cudaMalloc(&m->rlist, cap * sizeof(int));
-        if (e != cudaSuccess) { m->rcap = 0; return fail(GWN_ERR_OOM, "repair list allocation failed"); }
-        m->rcap = cap;
-    }
-    if (!m->rcount) {
-        cudaError_t e = cudaMalloc(&m->rcount, sizeof(int) * 4);
-        if (e != cudaSuccess) return fail(GWN_ERR_OOM, "repair counter allocation failed");
+// Bytes of the query workspace for n points of model m, and its layout.
+size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* ws) {
+    const long long cap = dim == 3 ? (long long)n * 96 + 65536 : 0;
+    const size_t cells = (size_t)1 << (dim == 2 ? 2 * kBinBits2 : 3 * kBinBits3);
+    const size_t hist = std::max(cells, (size_t)n_leaves) + 1;
+    const size_t keyn = std::max((size_t)n, (size_t)cap);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        char* p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~size_t(255);
+        return p;
+    };
+    Workspace w{};
+    w.perm = (int*)carve(n * sizeof(int));
+    w.key = (int*)carve(keyn * sizeof(int));
+    w.hist = (int*)carve(hist * sizeof(int));
+    w.wacc = (float*)carve(n * sizeof(float));
+    w.st = (uint32_t*)carve(n * sizeof(uint32_t));
+    w.pairs = (int2*)carve((size_t)cap * sizeof(int2));
+    w.pairs2 = (int2*)carve((size_t)cap * sizeof(int2));
+    w.counters = (int*)carve(8 * sizeof(int));
+    w.rpairs = (int2*)carve((dim == 3 ? (size_t)kRepairPairCap : 0) * sizeof(int2));
+    w.rw = (double*)carve(n * sizeof(double));
+    w.pairs64 = (int2*)carve((dim == 3 ? n : 0) * sizeof(int2));
+    w.rlist = (int*)carve(n * sizeof(int));
+    w.olist = (int*)carve((dim == 3 ? n : 0) * sizeof(int));
+    w.olist2 = (int*)carve((dim == 3 ? n : 0) * sizeof(int));
+    w.work = (unsigned long long*)carve(kWorkCount * sizeof(unsigned long long));
+    w.acc = (unsigned long long*)carve(8 * sizeof(unsigned long long));
+    w.pair_cap = cap;
+    if (ws) *ws = w;
+    return off;
+}
+
+constexpr size_t kChunk = (size_t)1 << 19;  // points per pass of the query pipeline
+
+gwn_status ensure_workspace(gwn_model_s* m, size_t n, size_t stage_bytes) {
+    n = std::min(n, kChunk);
+    if (n > m->ws_n || !m->ws_mem) {
+        size_t want = std::max<size_t>(n, 4096);
+        size_t bytes = workspace_layout(m->dim, m->host.n_leaves, want, nullptr, nullptr);
+        if (m->ws_mem) cudaFree(m->ws_mem);
+        m->ws_mem = nullptr;
+        cudaError_t e = cudaMalloc(&m->ws_mem, bytes);
+        if (e != cudaSuccess) { m->ws_n = 0; m->ws_bytes = 0; return fail(GWN_ERR_OOM, "query workspace allocation failed"); }
+        m->ws_bytes = bytes;
+        m->ws_n = want;
+        workspace_layout(m->dim, m->host.n_leaves, want, reinterpret_cast<char*>(m->ws_mem), &m->ws);
     }
     if (stage_bytes > m->stage_cap) {
         if (m->stage) cudaFree(m->stage);
@@ -361,43 +425,160 @@ gwn_status ensure_scratch(gwn_model_s* m, size_t n, size_t stage_bytes) {
 
 }  // namespace
 
-// Enqueue the query kernels on `st` for device-resident points/outputs.
-// Shared with the batched and serving entry points.
-gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
-                              uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, int* rlist,
-                              int* rcount) {
+// Enqueue the query kernels on `st` for device-resident points/outputs, using
+// workspace `ws` (sized for at least n points).  Shared with the batched and
+// serving entry points.
+static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
+                                uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const Workspace& ws) {
     QueryParams p;
+    p.work = qo.count_work ? ws.work : nullptr;
+    const int pc = m->prof_chunks;
+    const bool prof = qo.profile != 0 && pc < gwn_model_s::kMaxProfChunks;
+    cudaEvent_t* ev = prof ? m->ev[pc] : nullptr;
+    if (prof) {
+        if (!ev[0])
+            for (int k = 0; k < 4; ++k) GWN_CUDA_TRY(cudaEventCreate(&ev[k]));
+        m->prof_chunks = pc + 1;
+    }
     double beta = qo.beta > 0 ? qo.beta : m->opts.beta;
     p.beta2 = (float)(beta * beta);
+    double beta_leaf = qo.beta_leaf > 0 ? qo.beta_leaf : (m->opts.beta_leaf > 0 ? m->opts.beta_leaf : beta);
+    p.beta2_leaf = (float)(beta_leaf * beta_leaf);
     double br = m->opts.beta_repair;
-    if (br < 0) br = m->host.n_leaves <= 4096 ? 0.0 : 4.0 * beta;  // automatic choice
+    if (br < 0) br = m->host.n_leaves <= 4096 ? 0.0 : 2.0 * beta;  // automatic choice
     p.beta2_repair = br > 0 ? br * br : 0.0;
     p.band = (float)m->opts.repair_band;
     p.mode = qo.mode;
     p.precision = qo.precision >= 0 ? qo.precision : m->opts.precision;
     const int B = 128;
-    long long nb = ((long long)n + B - 1) / B;
+    const int ni = (int)n;
+    const unsigned nb = (unsigned)((n + B - 1) / B);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (p.precision == GWN_PREC_FP64) {
-        if (m->dim == 2) k_query64<2><<<(unsigned)nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status);
-        else k_query64<3><<<(unsigned)nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status);
+        if (p.mode == GWN_MODE_DIRECT) {
+            // exact FP64 direct sum, one warp per point (lanes stride over the leaves)
+            k_iota<<<nb, B, 0, st>>>(ni, ws.rlist, ws.counters + 1);
+            unsigned rb = (unsigned)std::min<long long>(((long long)n * 32 + B - 1) / B, (long long)sms * 16);
+            QueryParams pd = p;
+            pd.beta2_repair = 0.0;
+            if (m->dim == 2) k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, pd, out_w, out_label, out_status, ws.rlist, ws.counters + 1);
+            else k_repair<3><<<rb, B, 0, st>>>(m->tree, pts, dtype, pd, out_w, out_label, out_status, ws.rlist, ws.counters + 1);
+        } else {
+            if (m->dim == 2) k_query64<2><<<nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status);
+            else k_query64<3><<<nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status);
+        }
         GWN_CUDA_TRY(cudaGetLastError());
         return GWN_OK;
     }
-    GWN_CUDA_TRY(cudaMemsetAsync(rcount, 0, sizeof(int), st));
-    if (m->dim == 2)
-        k_query32<2><<<(unsigned)nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status, rlist, rcount);
-    else
-        k_query32<3><<<(unsigned)nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status, rlist, rcount);
-    GWN_CUDA_TRY(cudaGetLastError());
+    int* rcount = ws.counters + 1;
+    GWN_CUDA_TRY(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(int), st));
+    if (p.mode == GWN_MODE_DIRECT) {
+        if (m->dim == 2)
+            k_query32<2><<<nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status, ws.rlist, rcount);
+        else
+            k_query32<3><<<nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status, ws.rlist, rcount);
+        GWN_CUDA_TRY(cudaGetLastError());
+    } else {
+        // 1. spatial binning of the points (counting sort by Morton cell)
+        const int* perm = nullptr;
+        if (n >= 2048) {
+            const int bits = m->dim == 2 ? kBinBits2 : kBinBits3;
+            const int cells = 1 << (m->dim * bits);
+            float3 lo = make_float3((float)m->host.lo[0], (float)m->host.lo[1], (float)m->host.lo[2]);
+            float ex[3];
+            for (int k = 0; k < 3; ++k) {
+                double e = m->host.hi[k] - m->host.lo[k];
+                ex[k] = e > 0 ? (float)(1.0 / e) : 0.f;
+            }
+            float3 inv = make_float3(ex[0], ex[1], ex[2]);
+            GWN_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, (size_t)cells * sizeof(int), st));
+            if (m->dim == 2) k_bin<2><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, ws.key, ws.hist);
+            else k_bin<3><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, ws.key, ws.hist);
+            k_scan<<<1, 1024, 0, st>>>(ws.hist, cells);
+            k_scatter_perm<<<nb, B, 0, st>>>(ni, ws.key, ws.hist, ws.perm);
+            GWN_CUDA_TRY(cudaGetLastError());
+            perm = ws.perm;
+        }
+        // 2. traversal
+        if (prof) GWN_CUDA_TRY(cudaEventRecord(ev[0], st));
+        if (m->dim == 2) {
+            k_trav2<<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, perm, p.beta2, ws, p.work);
+            if (prof) {
+                GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
+                GWN_CUDA_TRY(cudaEventRecord(ev[2], st));
+                GWN_CUDA_TRY(cudaEventRecord(ev[3], st));
+            }
+        } else {
+            // rounds: round 0 over all points; rounds 1, 2 over the points whose
+            // (point, leaf) pairs did not fit the list in the previous round
+            const unsigned pb = (unsigned)std::max(1, sms * 16);
+            for (int round = 0; round < 3; ++round) {
+                const int* list = round == 0 ? perm : (round == 1 ? ws.olist : ws.olist2);
+                int* olist_out = round == 1 ? ws.olist2 : ws.olist;
+                k_trav3<<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
+                                          round == 0 ? nullptr : ws.counters + 5, olist_out);
+                if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
+                GWN_CUDA_TRY(cudaGetLastError());
+                // 3. exact leaves, grouped by leaf
+                GWN_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, (size_t)m->host.n_leaves * sizeof(int), st));
+                k_pair_key<<<pb, 256, 0, st>>>(ws.pair_cap, ws.counters, ws.pairs, ws.key, ws.hist);
+                k_scan<<<1, 1024, 0, st>>>(ws.hist, m->host.n_leaves);
+                k_pair_scatter<<<pb, 256, 0, st>>>(ws.pair_cap, ws.counters, ws.pairs, ws.key, ws.hist, ws.pairs2);
+                if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[2], st));
+                k_pair_eval<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters, ws.pairs2,
+                                                               ws.wacc, ws.st, ws.pairs64, ni, p.work);
+                if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[3], st));
+                k_pair_eval64<<<(unsigned)(sms * 2), B, 0, st>>>(m->tree, pts, dtype, ni, ws.counters, ws.pairs64, ws.wacc,
+                                                                 ws.st);
+                if (round < 2) k_next_round<<<1, 32, 0, st>>>(ws);
+            }
+            k_overflow3<<<(unsigned)(sms * 2), B, 0, st>>>(m->tree, pts, dtype, p.beta2, ws, ws.olist);
+        }
+        GWN_CUDA_TRY(cudaGetLastError());
+        // 4. outputs and the repair list
+        k_finish<<<nb, B, 0, st>>>(ni, ws.wacc, ws.st, p.precision, p.band, out_w, out_label, out_status, ws.rlist, rcount);
+        GWN_CUDA_TRY(cudaGetLastError());
+    }
     if (p.precision == GWN_PREC_FP32_REPAIR) {
-        int dev = 0, sms = 152;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         unsigned rb = (unsigned)std::min<long long>(std::max<long long>(nb, sms * 4), (long long)sms * 8);
         if (rb == 0) rb = 1;
-        if (m->dim == 2) k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, rlist, rcount);
-        else k_repair<3><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, rlist, rcount);
+        const unsigned wb = (unsigned)(sms * 4);  // blocks of kRepairWarps warps, one warp per repaired point
+        if (p.mode == GWN_MODE_DIRECT || !(p.beta2_repair > 0)) {
+            if (m->dim == 2) k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
+            else k_repair<3><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
+        } else if (m->dim == 2) {
+            k_rtrav_warp<2><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, p.beta2_repair, ws.rlist, ws, out_w,
+                                                             out_label, out_status);
+        } else {
+            k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, p.beta2_repair, ws.rlist, ws, out_w,
+                                                             out_label, out_status);
+            k_rpairs3<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.rlist, ws);
+            k_rfinish<<<(unsigned)(sms * 2), B, 0, st>>>(ws.rlist, ws, out_w, out_label, out_status);
+        }
         GWN_CUDA_TRY(cudaGetLastError());
+    }
+    k_accum<<<1, 32, 0, st>>>(ws);
+    GWN_CUDA_TRY(cudaGetLastError());
+    return GWN_OK;
+}
+
+// Enqueue a query on `st` for device-resident points and outputs, in chunks of
+// at most kChunk points (the workspace holds one chunk).
+gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
+                              uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const Workspace& ws) {
+    const size_t esz = (dtype == GWN_F32 ? sizeof(float) : sizeof(double)) * m->dim;
+    GWN_CUDA_TRY(cudaMemsetAsync(ws.acc, 0, 8 * sizeof(unsigned long long), st));
+    if (qo.count_work) GWN_CUDA_TRY(cudaMemsetAsync(ws.work, 0, kWorkCount * sizeof(unsigned long long), st));
+    m->prof_chunks = 0;
+    m->profiled = qo.profile != 0;
+    for (size_t off = 0; off < n; off += kChunk) {
+        size_t c = std::min(kChunk, n - off);
+        gwn_status s = enqueue_chunk(m, reinterpret_cast<const char*>(pts) + off * esz, dtype, c, out_w + off,
+                                     out_label ? out_label + off : nullptr, out_status ? out_status + off : nullptr,
+                                     qo, st, ws);
+        if (s != GWN_OK) return s;
     }
     return GWN_OK;
 }
@@ -417,6 +598,7 @@ void gwn_default_build_opts(gwn_build_opts* o) {
     o->device = -1;
     o->n_threads = 0;
     o->leaf_far = -1;
+    o->beta_leaf = 0.0;
 }
 
 void gwn_default_query_opts(gwn_query_opts* q) {
@@ -424,6 +606,139 @@ void gwn_default_query_opts(gwn_query_opts* q) {
     q->mode = GWN_MODE_BVH;
     q->precision = -1;
     q->beta = 0.0;
+    q->count_work = 0;
+    q->profile = 0;
+    q->beta_leaf = 0.0;
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// Picks the far-field factors (beta for internal nodes, beta_leaf for 3D
+// leaves) of a model: validation points -- uniform in the model's box, plus
+// points a little off the surface at random leaf centroids -- are evaluated
+// exactly (FP64 direct sum on the device), then with the FP32 path for every
+// candidate pair.  Among the pairs whose max |dGWN| stays below half the
+// tolerance, the one with the smallest counted work (flops per point) wins.
+
+__global__ void k_err(int n, const double* a, const double* b, double* out) {
+    __shared__ double smax[128];
+    double m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = fmax(m, fabs(a[i] - b[i]));
+    smax[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long*>(out), __double_as_longlong(smax[0]));
+}
+
+static gwn_status autotune(gwn_model_s* m) {
+    const int d = m->dim;
+    const HostModel& H = m->host;
+    const int nu = 768, nn = 256, nv = nu + nn;
+    std::vector<float> pts((size_t)nv * d);
+    uint64_t seed = 0x9e3779b97f4a7c15ull ^ (uint64_t)H.n_leaves;
+    auto rnd = [&]() {  // splitmix64
+        seed += 0x9e3779b97f4a7c15ull;
+        uint64_t z = seed;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int i = 0; i < nu; ++i)
+        for (int k = 0; k < d; ++k) pts[(size_t)i * d + k] = (float)(H.lo[k] + rnd() * (H.hi[k] - H.lo[k]));
+    double diag = 0;
+    for (int k = 0; k < d; ++k) diag += (H.hi[k] - H.lo[k]) * (H.hi[k] - H.lo[k]);
+    diag = std::sqrt(diag);
+    for (int i = nu; i < nv; ++i) {
+        int li = (int)(rnd() * H.n_leaves) % std::max(1, H.n_leaves);
+        for (int k = 0; k < d; ++k) {
+            double c = d == 3 ? (double)H.lhdr64[(size_t)li * 4 + k] : H.lhdr64[(size_t)li * 4 + k];
+            pts[(size_t)i * d + k] = (float)(c + (rnd() - 0.5) * 0.02 * diag);
+        }
+    }
+    float* dp = nullptr;
+    double *ref = nullptr, *w = nullptr, *err = nullptr;
+    GWN_CUDA_TRY(cudaMalloc(&dp, pts.size() * sizeof(float)));
+    GWN_CUDA_TRY(cudaMalloc(&ref, nv * sizeof(double)));
+    GWN_CUDA_TRY(cudaMalloc(&w, nv * sizeof(double)));
+    GWN_CUDA_TRY(cudaMalloc(&err, sizeof(double)));
+    GWN_CUDA_TRY(cudaMemcpy(dp, pts.data(), pts.size() * sizeof(float), cudaMemcpyHostToDevice));
+    gwn_status s = ensure_workspace(m, nv, 0);
+    gwn_query_opts qo;
+    gwn_default_query_opts(&qo);
+    qo.mode = GWN_MODE_DIRECT;
+    qo.precision = GWN_PREC_FP64;
+    if (s == GWN_OK) s = gwn_enqueue_device(m, dp, GWN_F32, nv, ref, nullptr, nullptr, qo, 0, m->ws);
+    const double betas[] = {2.0, 3.0, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0};
+    const double leafb[] = {2.0, 2.5, 3.0, 4.0, 6.0, 0.0};
+    double best_cost = 1e300, best_b = 0, best_bl = 0;
+    double fb_err = 1e300, fb_b = 0, fb_bl = 0;  // fallback: smallest error seen
+    const double tol = 0.5 * m->opts.tolerance;
+    for (double b : betas) {
+        bool any_ok = false;
+        for (double bl : leafb) {
+            if (s != GWN_OK) break;
+            if (d == 2 && bl != 0.0) continue;
+            if (bl > b) continue;
+            double blv = bl == 0.0 ? b : bl;
+            gwn_query_opts q2;
+            gwn_default_query_opts(&q2);
+            q2.precision = GWN_PREC_FP32;
+            q2.beta = b;
+            q2.beta_leaf = blv;
+            q2.count_work = 1;
+            s = gwn_enqueue_device(m, dp, GWN_F32, nv, w, nullptr, nullptr, q2, 0, m->ws);
+            if (s != GWN_OK) break;
+            cudaMemset(err, 0, sizeof(double));
+            k_err<<<4, 128>>>(nv, ref, w, err);
+            double e = 0;
+            unsigned long long wk[kWorkCount] = {}, acc[8] = {};
+            if (cudaMemcpy(&e, err, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(wk, m->ws.work, sizeof(wk), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(acc, m->ws.acc, sizeof(acc), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                s = fail(GWN_ERR_CUDA, "autotune readback failed");
+                break;
+            }
+            // a candidate whose exact-leaf pairs overflow the work list is rejected:
+            // its overflow path is slow and not counted
+            if (acc[3] + acc[6] > 0) continue;
+            if (e < fb_err) {
+                fb_err = e;
+                fb_b = b;
+                fb_bl = blv;
+            }
+            double cost = 10.0 * (wk[kWorkNodes] + wk[kWorkLeafTests]) + 72.0 * wk[kWorkFar] +
+                          28.0 * wk[kWorkGlDeg] + 70.0 * wk[kWorkGlNodes] + 2000.0 * wk[kWorkHits] +
+                          (d == 2 ? 60.0 * wk[kWorkLeaves] : 30.0 * wk[kWorkLeaves]);
+            if (std::getenv("GWN_AUTOTUNE_VERBOSE"))
+                std::fprintf(stderr, "[gwn autotune] leaves=%d beta=%.1f beta_leaf=%.1f max|dGWN|=%.3g flops/pt=%.3g\n",
+                             H.n_leaves, b, blv, e, cost / nv);
+            if (e <= tol) {
+                any_ok = true;
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_b = b;
+                    best_bl = blv;
+                }
+            }
+        }
+        if (any_ok && best_b > 0 && b > 2.0 * best_b) break;  // larger beta only costs more
+    }
+    cudaFree(dp);
+    cudaFree(ref);
+    cudaFree(w);
+    cudaFree(err);
+    if (s != GWN_OK) return s;
+    if (best_b == 0) {  // nothing met the tolerance: the most accurate candidate tried
+        best_b = fb_b > 0 ? fb_b : 8.0;
+        best_bl = fb_b > 0 ? fb_bl : 8.0;
+    }
+    m->opts.beta = best_b;
+    m->opts.beta_leaf = d == 3 ? best_bl : 0.0;
+    return GWN_OK;
 }
 
 static gwn_status build_common(int dim, const void* prims, size_t n, const gwn_build_opts* opts, gwn_model* out) {
@@ -465,8 +780,18 @@ static gwn_status build_common(int dim, const void* prims, size_t n, const gwn_b
     }
     DeviceGuard g(o.device);
     cudaGetDevice(&m->device);
+    bool tune = o.beta == 0.0;
+    if (tune) m->opts.beta = 2.0;
     s = finish_build(m, out);
     if (s != GWN_OK) return s;
+    if (tune) {
+        s = autotune(m);
+        if (s != GWN_OK) {
+            gwn_release(m);
+            *out = nullptr;
+            return s;
+        }
+    }
     m->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return GWN_OK;
 }
@@ -494,16 +819,17 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     if (qo.mode != GWN_MODE_BVH && qo.mode != GWN_MODE_DIRECT) return fail(GWN_ERR_INVALID_ARG, "unknown mode");
     if (qo.precision < -1 || qo.precision > 2) return fail(GWN_ERR_INVALID_ARG, "unknown precision");
     if (qo.beta != 0.0 && !(qo.beta >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta must be >= 2");
+    if (qo.beta_leaf != 0.0 && !(qo.beta_leaf >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_leaf must be >= 2");
     DeviceGuard g(m->device);
     std::lock_guard<std::mutex> lk(m->mu);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     size_t esz = dtype == GWN_F32 ? sizeof(float) : sizeof(double);
     size_t pbytes = n * m->dim * esz;
     size_t obytes = n * (sizeof(double) + sizeof(int32_t) + sizeof(uint32_t));
-    gwn_status s = ensure_scratch(m, n, mem == GWN_MEM_HOST ? pbytes + obytes + 64 : 0);
+    gwn_status s = ensure_workspace(m, n, mem == GWN_MEM_HOST ? pbytes + obytes + 64 : 0);
     if (s != GWN_OK) return s;
     if (mem == GWN_MEM_DEVICE)
-        return gwn_enqueue_device(m, points, dtype, n, out_w, out_label, (uint32_t*)out_status, qo, st, m->rlist, m->rcount);
+        return gwn_enqueue_device(m, points, dtype, n, out_w, out_label, (uint32_t*)out_status, qo, st, m->ws);
     // host buffers: stage through model-owned device memory
     char* base = reinterpret_cast<char*>(m->stage);
     void* dp = base;
@@ -511,13 +837,44 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     int32_t* dl = reinterpret_cast<int32_t*>(dw + n);
     uint32_t* ds = reinterpret_cast<uint32_t*>(dl + n);
     GWN_CUDA_TRY(cudaMemcpyAsync(dp, points, pbytes, cudaMemcpyHostToDevice, st));
-    s = gwn_enqueue_device(m, dp, dtype, n, dw, out_label ? dl : nullptr, out_status ? ds : nullptr, qo, st, m->rlist,
-                           m->rcount);
+    s = gwn_enqueue_device(m, dp, dtype, n, dw, out_label ? dl : nullptr, out_status ? ds : nullptr, qo, st, m->ws);
     if (s != GWN_OK) return s;
     GWN_CUDA_TRY(cudaMemcpyAsync(out_w, dw, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (out_label) GWN_CUDA_TRY(cudaMemcpyAsync(out_label, dl, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     if (out_status) GWN_CUDA_TRY(cudaMemcpyAsync(out_status, ds, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     GWN_CUDA_TRY(cudaStreamSynchronize(st));
+    return GWN_OK;
+}
+
+gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
+    if (!m || !out) return fail(GWN_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard g(m->device);
+    std::lock_guard<std::mutex> lk(m->mu);
+    unsigned long long c[8] = {};
+    unsigned long long wk[kWorkCount] = {};
+    if (m->ws_mem) {
+        GWN_CUDA_TRY(cudaDeviceSynchronize());
+        GWN_CUDA_TRY(cudaMemcpy(c, m->ws.acc, sizeof(c), cudaMemcpyDeviceToHost));
+        GWN_CUDA_TRY(cudaMemcpy(wk, m->ws.work, sizeof(wk), cudaMemcpyDeviceToHost));
+    }
+    for (int k = 0; k < 16; ++k) out[k] = 0;
+    for (int k = 0; k < 4; ++k) out[k] = (int64_t)c[k];
+    out[0] = (int64_t)(c[0] + c[7]);  // pairs over all rounds
+    out[3] = (int64_t)(c[6] + c[3]);  // points whose pairs overflowed in any round
+    for (int k = 0; k < kWorkCount; ++k) out[4 + k] = (int64_t)wk[k];
+    if (m->profiled) {
+        double a = 0, b = 0;
+        for (int ch = 0; ch < m->prof_chunks; ++ch) {
+            float x = 0, y = 0;
+            GWN_CUDA_TRY(cudaEventSynchronize(m->ev[ch][3]));
+            GWN_CUDA_TRY(cudaEventElapsedTime(&x, m->ev[ch][0], m->ev[ch][1]));
+            GWN_CUDA_TRY(cudaEventElapsedTime(&y, m->ev[ch][2], m->ev[ch][3]));
+            a += x;
+            b += y;
+        }
+        out[12] = (int64_t)(a * 1000.0);
+        out[13] = (int64_t)(b * 1000.0);
+    }
     return GWN_OK;
 }
 
@@ -539,6 +896,7 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
         s->lo[k] = m->host.lo[k];
         s->hi[k] = m->host.hi[k];
     }
+    s->beta_leaf = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
     return GWN_OK;
 }
 

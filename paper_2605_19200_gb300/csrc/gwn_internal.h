@@ -62,9 +62,11 @@ struct Leaf3Info {
     int32_t c2_off, c2_cnt;    // 2D boundary curves in local (u, v) for the trim membership test
 };
 
-// A 3D boundary curve: rational Bezier of degree deg (<= kMaxC3Deg) stored as
-// deg + 1 homogeneous points starting at ctrl_off in the curve-point array,
-// counted `mult` times (winding multiplicity of a clipped rectangle edge).
+// A 3D boundary curve: rational Bezier of degree D = deg (<= kMaxC3Deg) stored
+// from ctrl_off in the curve-point array as D + 1 homogeneous points scaled by
+// their binomial coefficients C(D, i) c_i, followed by the D derivative points
+// C(D-1, i) (c_{i+1} - c_i), and counted `mult` times (winding multiplicity of a
+// clipped rectangle edge).
 constexpr int kMaxC3Deg = 18;
 struct Curve3Info {
     int32_t ctrl_off;
@@ -108,8 +110,28 @@ struct DevTree {
     const float* c2mult;
 };
 
+// Work counters (only when QueryParams::work != nullptr): the algorithmic
+// units of the roofline numerator, see the design doc.
+enum {
+    kWorkNodes = 0,      // internal nodes visited (far test)
+    kWorkLeafTests = 1,  // leaves visited (far test or direct)
+    kWorkFar = 2,        // Taylor evaluations (nodes and leaves)
+    kWorkLeaves = 3,     // exact leaf evaluations
+    kWorkGlNodes = 4,    // Gauss-Legendre nodes of 3D boundary integrals
+    kWorkGlDeg = 5,      // sum over those nodes of the curve degree D
+    kWorkHits = 6,       // foot-point searches (3D near leaves)
+    kWorkChords = 7,     // chord angles (2D leaf pieces)
+    kWorkCount = 8
+};
+
+struct WorkLocal {
+    unsigned long long v[kWorkCount];
+};
+
 struct QueryParams {
-    float beta2;               // beta^2 of the FP32 pass
+    unsigned long long* work;  // nullptr: no counting
+    float beta2;               // beta^2 of the FP32 pass (internal nodes)
+    float beta2_leaf;          // beta^2 of the leaves' own far test (3D)
     double beta2_repair;       // beta^2 of the FP64 repair pass; <= 0: direct sum
     float band;                // repair band around half-integers
     int mode;                  // GWN_MODE_*

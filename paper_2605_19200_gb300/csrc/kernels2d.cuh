@@ -193,18 +193,21 @@ GWN_HD inline T far2_eval(const T* f, T rx, T ry) {
 }
 
 // Algorithm 1 for one 2D query, FP32.
-GWN_HD float query2_32(const DevTree& t, float qx, float qy, float beta2, uint32_t& st) {
+GWN_HD float query2_32(const DevTree& t, float qx, float qy, float beta2, uint32_t& st, WorkLocal* wl = nullptr) {
     float w = 0.f;
     int stack[kStack32];
     int sp = 0;
     int node = t.root;
     while (true) {
         if (node < 0) {
+            if (wl) wl->v[kWorkLeaves] += 1;
             w += leaf2_eval32(t, ~node, qx, qy, st);
         } else {
+            if (wl) wl->v[kWorkNodes] += 1;
             float4 h = GWN_LDG(t.hdr + node);
             float rx = h.x - qx, ry = h.y - qy;
             if (rx * rx + ry * ry > beta2 * h.w) {
+                if (wl) wl->v[kWorkFar] += 1;
                 const float4* M = t.mom + (size_t)node * kMom2Vec;
                 float4 a = GWN_LDG(M), b = GWN_LDG(M + 1), c = GWN_LDG(M + 2);
                 float f[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};

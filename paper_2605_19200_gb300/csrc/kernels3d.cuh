@@ -21,7 +21,7 @@
 //     boundary).
 //   The line integral uses 8-point Gauss-Legendre panels, bisected (stackless,
 //   by level and index) until each panel is shorter than PanelRatio times its
-//   distance to q.  FP32 stops at kLevel32 bisections; a leaf that needs more, or
+//   distance to q and to the string.  FP32 stops at kLevel32 bisections; a leaf that needs more, or
 //   whose foot point is too close to call in FP32, is evaluated again in FP64:
 //   the near-boundary band.
 // far3: the order-2 Taylor expansion of Eq. 3 in folded form (gwn_internal.h).
@@ -34,29 +34,37 @@
 namespace gwn {
 
 constexpr int kLevel32 = 10;
-constexpr int kLevel64 = 40;
+constexpr int kLevel64 = 30;
 // panel length / distance-to-q bound of the 8-point rule: the quadrature error
 // of an analytic integrand decays like rho^-16 with rho the Bernstein-ellipse
-// parameter, ~3.0 at 1.5 (FP32, ~1e-8 relative) and ~6.7 at 0.6 (FP64, ~1e-13)
+// parameter, ~3.0 at 1.5 (FP32); FP64 uses 0.5, which measured ~1e-8 against
+// the oracle where 1.0 gave ~1e-7
 template <typename T> struct PanelRatio;
 template <> struct PanelRatio<float> { static constexpr float v = 1.5f; };
-template <> struct PanelRatio<double> { static constexpr double v = 0.6; };
+template <> struct PanelRatio<double> { static constexpr double v = 0.5; };
 
 // binomial coefficients and the 8-point Gauss-Legendre rule on [0, 1]: device
 // constant memory, with host mirrors for host-side execution
 __constant__ float c_binom[kMaxC3Deg + 1][kMaxC3Deg + 1];
 __constant__ double c_glx8[8];
 __constant__ double c_glw8[8];
+__constant__ float c_glx8f[8];
+__constant__ float c_glw8f[8];
 static float h_binom[kMaxC3Deg + 1][kMaxC3Deg + 1];
 static double h_glx8[8], h_glw8[8];
+static float h_glx8f[8], h_glw8f[8];
 #if defined(__CUDA_ARCH__)
 #define GWN_BINOM(d, i) c_binom[d][i]
 #define GWN_GLX(k) c_glx8[k]
 #define GWN_GLW(k) c_glw8[k]
+#define GWN_GLXF(k) c_glx8f[k]
+#define GWN_GLWF(k) c_glw8f[k]
 #else
 #define GWN_BINOM(d, i) h_binom[d][i]
 #define GWN_GLX(k) h_glx8[k]
 #define GWN_GLW(k) h_glw8[k]
+#define GWN_GLXF(k) h_glx8f[k]
+#define GWN_GLWF(k) h_glw8f[k]
 #endif
 
 // accessors of one leaf's geometry, in FP32 (relative to the leaf centre) or FP64 (absolute)
@@ -83,29 +91,30 @@ struct Geo64 {
     }
 };
 
-// value and derivative (homogeneous) of a degree-D Bernstein curve by Horner's rule
+// value and derivative (homogeneous) of a degree-D Bernstein curve by Horner's
+// rule in r = a / (1 - a), a = min(t, 1 - t) (the curve is read backwards when
+// t > 1/2), with the binomial-scaled points P_i = C(D,i) c_i and derivative
+// points Q_i = C(D-1,i) (c_{i+1} - c_i) stored by the build:
+//   X(t)  = (1 - a)^D     sum_i P_i r^i
+//   X'(t) = D (1 - a)^(D-1) sum_i Q_i r^i
 template <typename T, typename G>
 GWN_HD inline void bern4(const G& g, int D, T t, T X[4], T dX[4]) {
     const bool rev = t > T(0.5);
     const T a = rev ? T(1) - t : t;
     const T b = T(1) - a;
     const T r = a / b;
-    T acc[4] = {0, 0, 0, 0}, dacc[4] = {0, 0, 0, 0};
-    T hi[4], lo[4];
-    // value: sum_i C(D,i) c_i a^i b^(D-i), walked from i = D down to 0
-    g.pt(rev ? 0 : D, hi);
-    for (int c = 0; c < 4; ++c) acc[c] = hi[c];
+    T acc[4], dacc[4], h[4];
+    g.pt(rev ? 0 : D, acc);
     for (int i = D - 1; i >= 0; --i) {
-        g.pt(rev ? D - i : i, lo);
-        T cb = (T)GWN_BINOM(D, i);
-        T cd = (T)GWN_BINOM(D - 1, i);
-        for (int c = 0; c < 4; ++c) {
-            dacc[c] = (i == D - 1) ? (hi[c] - lo[c]) : dacc[c] * r + cd * (hi[c] - lo[c]);
-            acc[c] = acc[c] * r + cb * lo[c];
-            hi[c] = lo[c];
-        }
+        g.pt(rev ? D - i : i, h);
+        for (int c = 0; c < 4; ++c) acc[c] = acc[c] * r + h[c];
     }
-    // scale by b^D and b^(D-1)
+    g.pt(D + 1 + (rev ? 0 : D - 1), dacc);
+    for (int i = D - 2; i >= 0; --i) {
+        g.pt(D + 1 + (rev ? D - 1 - i : i), h);
+        for (int c = 0; c < 4; ++c) dacc[c] = dacc[c] * r + h[c];
+    }
+    // b^(D-1) by repeated squaring
     T pw = T(1), base = b;
     int e = D - 1;
     while (e > 0) {
@@ -113,17 +122,16 @@ GWN_HD inline void bern4(const G& g, int D, T t, T X[4], T dX[4]) {
         base *= base;
         e >>= 1;
     }
-    T sgn = rev ? T(-1) : T(1);
     for (int c = 0; c < 4; ++c) {
         X[c] = acc[c] * pw * b;
-        dX[c] = sgn * T(D) * dacc[c] * pw;
+        dX[c] = T(D) * dacc[c] * pw;
     }
 }
 
 template <typename T> struct Gl8;
 template <> struct Gl8<float> {
-    static GWN_HD inline float x(int k) { return (float)GWN_GLX(k); }
-    static GWN_HD inline float w(int k) { return (float)GWN_GLW(k); }
+    static GWN_HD inline float x(int k) { return GWN_GLXF(k); }
+    static GWN_HD inline float w(int k) { return GWN_GLWF(k); }
 };
 template <> struct Gl8<double> {
     static GWN_HD inline double x(int k) { return GWN_GLX(k); }
@@ -133,12 +141,13 @@ template <> struct Gl8<double> {
 // int A_s(x(t) - q) . x'(t) dt over one boundary curve, adaptive; sets deep if
 // the panel limit was hit
 template <typename T, typename G>
-GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int maxlevel, bool& deep) {
+GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int maxlevel, bool& deep,
+                             WorkLocal* wl = nullptr) {
     T acc = 0;
     int level = 0;
-    unsigned long long idx = 0;
+    unsigned idx = 0;  // panel index at `level` (levels stay below 32)
     while (true) {
-        const T h = T(1) / T(1ull << level);
+        const T h = T(1) / T(1u << level);
         const T a = T(idx) * h;
         T psum = 0, dmin2 = T(1e30), len = 0;
         T px = 0, py = 0, pz = 0;
@@ -154,14 +163,22 @@ GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int 
             T rn = sqrt(rr);
             T sr = s[0] * r0 + s[1] * r1 + s[2] * r2;
             T c0 = s[1] * r2 - s[2] * r1, c1 = s[2] * r0 - s[0] * r2, c2 = s[0] * r1 - s[1] * r0;
-            T f = (c0 * d0 + c1 * d1 + c2 * d2) / (rn * (rn + sr));
+            T den = rn * (rn + sr);
+            T f = (c0 * d0 + c1 * d1 + c2 * d2) / den;
             psum += Gl8<T>::w(k) * f;
-            dmin2 = fmin(dmin2, rr);
+            // the integrand is singular at q and along the string {q - t s}; near
+            // the string |r| (|r| + s.r) ~ (distance to the string)^2 / 2, so the
+            // panel must be short relative to both distances
+            dmin2 = fmin(dmin2, fmin(rr, T(2) * den));
             if (k > 0) {
                 T e0 = x0 - px, e1 = x1 - py, e2 = x2 - pz;
                 len += sqrt(e0 * e0 + e1 * e1 + e2 * e2);
             }
             px = x0; py = x1; pz = x2;
+        }
+        if (wl) {
+            wl->v[kWorkGlNodes] += 8;
+            wl->v[kWorkGlDeg] += 8ull * (unsigned long long)D;
         }
         // the 8 nodes span ~96% of the panel
         len *= T(1.1);
@@ -173,7 +190,7 @@ GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int 
         }
         if (refine) deep = true;
         acc += psum * h;
-        while (idx & 1ull) {
+        while (idx & 1u) {
             idx >>= 1;
             --level;
         }
@@ -354,7 +371,9 @@ GWN_HD int leaf_hit(const DevTree& t, const Leaf3Info& I, const G& g, const T q[
 // GWN of leaf li at q (q relative to the leaf geometry's origin); false if the
 // precision of T could not resolve it
 template <typename T, typename G>
-GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T q[3], T* out, int maxlevel) {
+GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T q[3], T* out, int maxlevel,
+                       WorkLocal* wl = nullptr) {
+    if (wl) wl->v[kWorkLeaves] += 1;
     T nrm[3] = {(T)I.nrm[0], (T)I.nrm[1], (T)I.nrm[2]};
     T cen[3];
     if (sizeof(T) == 4) {
@@ -373,6 +392,7 @@ GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T
     } else {
         T sig = (dq[0] * nrm[0] + dq[1] * nrm[1] + dq[2] * nrm[2]) >= 0 ? T(1) : T(-1);
         s[0] = -sig * nrm[0]; s[1] = -sig * nrm[1]; s[2] = -sig * nrm[2];
+        if (wl) wl->v[kWorkHits] += 1;
         int hr = leaf_hit<T>(t, I, g, q, nrm, sig, (T)I.diag, &hits, sizeof(T) == 4 ? kNear32 : kMaxLevel64);
         if (hr == kHitUnsure) return false;
     }
@@ -383,7 +403,7 @@ GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T
         G gc = g;
         if (sizeof(T) == 4) gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts + ci.ctrl_off);
         else gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts64 + (size_t)ci.ctrl_off * 4);
-        acc += (T)ci.mult * curve_line_integral<T>(gc, ci.deg, q, s, maxlevel, deep);
+        acc += (T)ci.mult * curve_line_integral<T>(gc, ci.deg, q, s, maxlevel, deep, wl);
     }
     if (deep) return false;
     *out = acc * T(0.07957747154594767) - hits;  // 1 / (4 pi)
@@ -399,12 +419,19 @@ GWN_HD inline double leaf3_eval64(const DevTree& t, int li, double qx, double qy
     return w;
 }
 
-GWN_HD inline float leaf3_eval32(const DevTree& t, int li, float qx, float qy, float qz, uint32_t& st) {
+// FP32 evaluation only; false if the leaf needs the FP64 near band
+GWN_HD inline bool leaf3_try32(const DevTree& t, int li, float qx, float qy, float qz, float* w,
+                               WorkLocal* wl = nullptr) {
     Leaf3Info I = t.leaf3[li];
     Geo32 g{t.net3 + (size_t)li * kNet3Vec, nullptr};
     float q[3] = {qx - I.cen[0], qy - I.cen[1], qz - I.cen[2]};
-    float w = 0;
-    if (leaf3_core<float>(t, I, g, q, &w, kLevel32)) return w;
+    *w = 0.f;
+    return leaf3_core<float>(t, I, g, q, w, kLevel32, wl);
+}
+
+GWN_HD inline float leaf3_eval32(const DevTree& t, int li, float qx, float qy, float qz, uint32_t& st) {
+    float w;
+    if (leaf3_try32(t, li, qx, qy, qz, &w)) return w;
     st |= GWN_QS_NEAR;
     return (float)leaf3_eval64(t, li, (double)qx, (double)qy, (double)qz, st);
 }
@@ -430,8 +457,9 @@ GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz) {
     return far3_eval<float>(f, rx, ry, rz);
 }
 
-// Algorithm 1 for one 3D query, FP32
-GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float beta2, uint32_t& st) {
+// Algorithm 1 for one 3D query, FP32 (beta2l: the leaves' far test, <= 0 means beta2)
+GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float beta2, uint32_t& st, float beta2l = 0.f) {
+    if (!(beta2l > 0.f)) beta2l = beta2;
     float w = 0.f;
     int stack[kStack32];
     int sp = 0;
@@ -443,7 +471,7 @@ GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float bet
             if (t.leaf_far) {
                 float4 h = GWN_LDG(t.lhdr + li);
                 float rx = h.x - qx, ry = h.y - qy, rz = h.z - qz;
-                if (rx * rx + ry * ry + rz * rz > beta2 * h.w) {
+                if (rx * rx + ry * ry + rz * rz > beta2l * h.w) {
                     w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
                     done = true;
                 }

@@ -1,0 +1,559 @@
+// query_pipeline.cuh -- the batched query as a sequence of kernels on one stream.
+//
+//  1. Spatial binning: each point gets the Morton code of its cell in a
+//     2^kBinBits-per-axis grid over the model's box; a counting sort by cell
+//     yields a permutation, so the threads of a warp traverse the tree for
+//     nearby points and take mostly the same branches.
+//  2. Traversal (Algorithm 1): far nodes (and, in 3D, far leaves) add their
+//     Taylor term (Eq. 3) to the point's accumulator.  2D leaves are evaluated
+//     in place (one atan2 unless the point is inside the leaf's box).  3D leaves
+//     that need the exact evaluation are not evaluated in the traversal: the
+//     (point, leaf) pair is appended to a work list, with one atomic per warp.
+//  3. 3D only: the work list is counting-sorted by leaf, and one thread per pair
+//     evaluates the leaf and adds it to the point's accumulator.  Consecutive
+//     threads now share the same leaf, so a warp reads one set of boundary
+//     curves and runs the same quadrature panels.
+//  4. Finish: value, label and status per point; points whose value lies within
+//     the repair band of a half-integer, or that were flagged, are appended to
+//     the FP64 repair list.
+#pragma once
+
+#include "gwn_internal.h"
+#include "kernels2d.cuh"
+#include "kernels3d.cuh"
+
+namespace gwn {
+
+constexpr int kBinBits2 = 9;   // 512 x 512 cells in 2D
+constexpr int kBinBits3 = 6;   // 64^3 cells in 3D
+constexpr int kPairLocal = 8;  // pairs a thread buffers before reserving space
+constexpr uint32_t kPairOverflow = 0x100u;  // internal status bit: the point's pairs did not fit
+
+constexpr long long kRepairPairCap = 1ll << 22;  // FP64 repair pairs per chunk
+
+struct Workspace {
+    int2* pairs64;    // near-band pairs (capacity n)
+    int2* rpairs;     // FP64 repair pairs (kRepairPairCap, 3D)
+    double* rw;       // FP64 repair accumulators (n)
+    int* perm;        // n
+    int* key;         // max(n, pair capacity)
+    int* hist;        // max(cells, n_leaves) + 1
+    float* wacc;      // n
+    uint32_t* st;     // n
+    int2* pairs;      // pair capacity
+    int2* pairs2;     // pair capacity (sorted)
+    int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
+                      // [5] overflowed points of the current round (list input), [6] total overflow,
+                      // [7] pairs of finished rounds
+    int* olist;       // n: points whose pairs did not fit (rounds alternate with olist2)
+    int* olist2;      // n
+    unsigned long long* work;  // kWorkCount counters
+    unsigned long long* acc;   // per-query totals of counters[0..7] over all chunks
+    int* rlist;       // n
+    long long pair_cap;
+};
+
+__device__ __forceinline__ uint32_t spread_bits2(uint32_t x) {
+    x &= 0x0000ffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+__device__ __forceinline__ uint32_t spread_bits3(uint32_t x) {
+    x &= 0x000003ffu;
+    x = (x | (x << 16)) & 0xff0000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__device__ __forceinline__ void flush_work(const WorkLocal& wl, unsigned long long* work) {
+    for (int k = 0; k < kWorkCount; ++k)
+        if (wl.v[k]) atomicAdd(&work[k], wl.v[k]);
+}
+
+__device__ __forceinline__ void load_point_f(const void* pts, int dtype, int dim, long long i, float* q) {
+    if (dtype == GWN_F32) {
+        const float* p = reinterpret_cast<const float*>(pts) + i * dim;
+        for (int k = 0; k < dim; ++k) q[k] = p[k];
+    } else {
+        const double* p = reinterpret_cast<const double*>(pts) + i * dim;
+        for (int k = 0; k < dim; ++k) q[k] = (float)p[k];
+    }
+}
+
+template <int DIM>
+__global__ void k_bin(const void* pts, int dtype, int n, float3 lo, float3 inv, int* key, int* hist) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float q[3] = {0, 0, 0};
+    load_point_f(pts, dtype, DIM, i, q);
+    const int bits = DIM == 2 ? kBinBits2 : kBinBits3;
+    const float cells = (float)(1 << bits);
+    float l[3] = {lo.x, lo.y, lo.z}, s[3] = {inv.x, inv.y, inv.z};
+    uint32_t c[3];
+    for (int k = 0; k < DIM; ++k) {
+        float t = (q[k] - l[k]) * s[k] * cells;
+        t = fminf(fmaxf(t, 0.f), cells - 1.f);
+        c[k] = (uint32_t)t;
+    }
+    int code = DIM == 2 ? (int)(spread_bits2(c[0]) | (spread_bits2(c[1]) << 1))
+                        : (int)(spread_bits3(c[0]) | (spread_bits3(c[1]) << 1) | (spread_bits3(c[2]) << 2));
+    key[i] = code;
+    atomicAdd(&hist[code], 1);
+}
+
+// exclusive scan of hist[0..K) in place by one block
+__global__ void k_scan(int* hist, int K) {
+    __shared__ int part[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < K; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < K ? hist[i] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < K) hist[i] = carry + part[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+}
+
+__global__ void k_scatter_perm(int n, const int* key, int* cursor, int* perm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int pos = atomicAdd(&cursor[key[i]], 1);
+    perm[pos] = i;
+}
+
+// append (point, leaf) pairs from a converged warp: one atomic per warp.  If
+// the list is full the point is flagged; such points skip the pair pass and are
+// evaluated again, leaves in place, by k_overflow3.
+__device__ __forceinline__ void flush_pairs(int2* local, int cnt, Workspace ws, uint32_t& st, unsigned mask) {
+    int lane = threadIdx.x & 31;
+    int incl = cnt;
+    for (int off = 1; off < 32; off <<= 1) {
+        int v = __shfl_up_sync(mask, incl, off);
+        if (lane >= off) incl += v;
+    }
+    int total = __shfl_sync(mask, incl, 31);
+    int base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(&ws.counters[0], total);
+    base = __shfl_sync(mask, base, 31);
+    long long start = (long long)base + incl - cnt;
+    for (int k = 0; k < cnt; ++k) {
+        if (start + k < ws.pair_cap) ws.pairs[start + k] = local[k];
+        else st |= kPairOverflow;
+    }
+}
+
+// traversal with deferred 3D leaves; every thread of the grid reaches the
+// warp-wide flushes (out-of-range threads take part with no pairs)
+// n_dev != nullptr: the point list `perm` holds *n_dev entries (a later round
+// over the points whose pairs overflowed; their indices go to `olist_out`)
+__global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int dtype, int n, const int* perm,
+                                               float beta2, float beta2l, Workspace ws, unsigned long long* work,
+                                               const int* n_dev, int* olist_out) {
+    WorkLocal wl = {};
+    if (n_dev) n = *n_dev;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev && blockIdx.x * blockDim.x >= n) return;  // whole block past the list
+    bool active = i < n;
+    int qi = active ? (perm ? perm[i] : i) : 0;
+    float q[3] = {0, 0, 0};
+    if (active) load_point_f(pts, dtype, 3, qi, q);
+    float w = 0.f;
+    uint32_t st = 0;
+    int2 local[kPairLocal];
+    int cnt = 0;
+    int stack[kStack32];
+    int sp = 0;
+    int node = active ? t.root : 0;
+    bool running = active;
+    while (__any_sync(0xffffffffu, running)) {
+        if (running) {
+            bool pop = true;
+            if (node < 0) {
+                int li = ~node;
+                float4 h = GWN_LDG(t.lhdr + li);
+                float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
+                if (work) wl.v[kWorkLeafTests] += 1;
+                if (t.leaf_far && rx * rx + ry * ry + rz * rz > beta2l * h.w) {
+                    if (work) wl.v[kWorkFar] += 1;
+                    w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
+                } else {
+                    local[cnt++] = make_int2(qi, li);
+                }
+            } else {
+                float4 h = GWN_LDG(t.hdr + node);
+                float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
+                if (work) wl.v[kWorkNodes] += 1;
+                if (rx * rx + ry * ry + rz * rz > beta2 * h.w) {
+                    if (work) wl.v[kWorkFar] += 1;
+                    w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz);
+                } else {
+                    int2 ch = GWN_LDG(t.child + node);
+                    if (sp < kStack32) stack[sp++] = ch.y; else st |= GWN_QS_STACK_OVERFLOW;
+                    node = ch.x;
+                    pop = false;
+                }
+            }
+            if (pop) {
+                if (sp == 0) running = false;
+                else node = stack[--sp];
+            }
+        }
+        // flush when any lane's buffer is full (warp-uniform decision)
+        if (__any_sync(0xffffffffu, cnt == kPairLocal)) {
+            flush_pairs(local, cnt, ws, st, 0xffffffffu);
+            cnt = 0;
+        }
+    }
+    flush_pairs(local, cnt, ws, st, 0xffffffffu);
+    if (active) {
+        ws.wacc[qi] = w;
+        ws.st[qi] = st;
+        if (st & kPairOverflow) olist_out[atomicAdd(&ws.counters[3], 1)] = qi;
+    }
+    if (work) flush_work(wl, work);
+}
+
+// points whose pairs still overflowed after the last round: whole traversal
+// again, leaves in place
+__global__ void __launch_bounds__(128) k_overflow3(DevTree t, const void* pts, int dtype, float beta2, Workspace ws,
+                                                   const int* list) {
+    int cnt = ws.counters[3];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        int qi = list[k];
+        float q[3];
+        load_point_f(pts, dtype, 3, qi, q);
+        uint32_t st = 0;
+        ws.wacc[qi] = query3_32(t, q[0], q[1], q[2], beta2, st);
+        ws.st[qi] = st;
+    }
+}
+
+__global__ void k_pair_key(long long npair_cap, const int* counters, const int2* pairs, int* key, int* hist) {
+    long long np = min((long long)counters[0], npair_cap);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
+        int leaf = pairs[k].y;
+        key[k] = leaf;
+        atomicAdd(&hist[leaf], 1);
+    }
+}
+
+__global__ void k_pair_scatter(long long npair_cap, const int* counters, const int2* pairs, const int* key, int* cursor,
+                               int2* out) {
+    long long np = min((long long)counters[0], npair_cap);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
+        int pos = atomicAdd(&cursor[key[k]], 1);
+        out[pos] = pairs[k];
+    }
+}
+
+__global__ void __launch_bounds__(128) k_pair_eval(DevTree t, const void* pts, int dtype, long long npair_cap,
+                                                   int* counters, const int2* pairs, float* wacc, uint32_t* st,
+                                                   int2* pairs64, int npair64_cap, unsigned long long* work) {
+    WorkLocal wl = {};
+    long long np = min((long long)counters[0], npair_cap);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
+        int2 pr = pairs[k];
+        if (st[pr.x] & kPairOverflow) continue;  // recomputed by k_overflow3
+        float q[3];
+        load_point_f(pts, dtype, 3, pr.x, q);
+        float v;
+        if (leaf3_try32(t, pr.y, q[0], q[1], q[2], &v, work ? &wl : nullptr)) {
+            atomicAdd(&wacc[pr.x], v);
+        } else {
+            int slot = atomicAdd(&counters[2], 1);
+            if (slot < npair64_cap) pairs64[slot] = pr;
+            atomicOr(&st[pr.x], slot < npair64_cap ? GWN_QS_NEAR : GWN_QS_STACK_OVERFLOW);
+        }
+    }
+    if (work) flush_work(wl, work);
+}
+
+// the near band: leaves that FP32 could not resolve, in FP64
+__global__ void k_pair_eval64(DevTree t, const void* pts, int dtype, int npair64_cap, const int* counters,
+                              const int2* pairs64, float* wacc, uint32_t* st) {
+    int np = min(counters[2], npair64_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
+        int2 pr = pairs64[k];
+        double q[3];
+        if (dtype == GWN_F32) {
+            const float* p = reinterpret_cast<const float*>(pts) + (size_t)pr.x * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        } else {
+            const double* p = reinterpret_cast<const double*>(pts) + (size_t)pr.x * 3;
+            q[0] = (double)(float)p[0]; q[1] = (double)(float)p[1]; q[2] = (double)(float)p[2];
+        }
+        uint32_t s = 0;
+        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s);
+        atomicAdd(&wacc[pr.x], (float)v);
+        if (s) atomicOr(&st[pr.x], s);
+    }
+}
+
+// 2D traversal (leaves evaluated in place) in binned order
+__global__ void __launch_bounds__(128) k_trav2(DevTree t, const void* pts, int dtype, int n, const int* perm,
+                                               float beta2, Workspace ws, unsigned long long* work) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int qi = perm ? perm[i] : i;
+    float q[2];
+    load_point_f(pts, dtype, 2, qi, q);
+    uint32_t st = 0;
+    WorkLocal wl = {};
+    float w = query2_32(t, q[0], q[1], beta2, st, work ? &wl : nullptr);
+    if (work) flush_work(wl, work);
+    ws.wacc[qi] = w;
+    ws.st[qi] = st;
+}
+
+__global__ void k_finish(int n, const float* wacc, const uint32_t* stv, int precision, float band, double* out_w,
+                         int* out_label, uint32_t* out_status, int* rlist, int* rcount) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double w = (double)wacc[i];
+    uint32_t st = stv[i];
+    if (precision == GWN_PREC_FP32_REPAIR) {
+        double fr = w - floor(w);
+        if (fabs(fr - 0.5) < (double)band || (st & (GWN_QS_STACK_OVERFLOW | GWN_QS_UNRESOLVED))) {
+            int slot = atomicAdd(rcount, 1);
+            rlist[slot] = i;
+        }
+    }
+    out_w[i] = w;
+    if (out_label) out_label[i] = (int)round(w);
+    if (out_status) out_status[i] = st;
+}
+
+}  // namespace gwn
+
+namespace gwn {
+
+// ---- FP64 repair of the listed points (3D), with the same deferral as the
+// FP32 pass: one thread per point traverses in FP64 (beta_repair), adds far
+// terms and defers exact leaves to a pair list; one thread per pair then
+// evaluates the leaf in FP64.  Points whose pairs overflow the list evaluate
+// them in place.
+__global__ void __launch_bounds__(128) k_rtrav3(DevTree t, const void* pts, int dtype, double beta2r, const int* rlist,
+                                                Workspace ws) {
+    int cnt = ws.counters[1];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        int qi = rlist[k];
+        double q[3];
+        if (dtype == GWN_F32) {
+            const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        } else {
+            const double* p = reinterpret_cast<const double*>(pts) + (size_t)qi * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        }
+        double w = 0.0;
+        uint32_t st = 0;
+        int stack[kStack64];
+        int sp = 0;
+        int node = t.root;
+        while (true) {
+            if (node < 0) {
+                int li = ~node;
+                const double* h = t.lhdr64 + (size_t)li * 4;
+                double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
+                if (beta2r > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2r * h[3]) {
+                    w += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
+                } else {
+                    long long slot = atomicAdd(&ws.counters[4], 1);
+                    if (slot < kRepairPairCap) ws.rpairs[slot] = make_int2(k, li);
+                    else w += leaf3_eval64(t, li, q[0], q[1], q[2], st);
+                }
+            } else {
+                const double* h = t.hdr64 + (size_t)node * 4;
+                double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
+                if (beta2r > 0 && rx * rx + ry * ry + rz * rz > beta2r * h[3]) {
+                    w += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz);
+                } else {
+                    int2 ch = t.child[node];
+                    if (sp < kStack64) stack[sp++] = ch.y; else st |= GWN_QS_UNRESOLVED;
+                    node = ch.x;
+                    continue;
+                }
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+        ws.rw[k] = w;
+        ws.st[qi] = st;  // the FP32 pass's flags are replaced by the repair's
+    }
+}
+
+__global__ void __launch_bounds__(128) k_rpairs3(DevTree t, const void* pts, int dtype, const int* rlist, Workspace ws) {
+    long long np = min((long long)ws.counters[4], kRepairPairCap);
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+        int2 pr = ws.rpairs[j];
+        int qi = rlist[pr.x];
+        double q[3];
+        if (dtype == GWN_F32) {
+            const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        } else {
+            const double* p = reinterpret_cast<const double*>(pts) + (size_t)qi * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        }
+        uint32_t s = 0;
+        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s);
+        atomicAdd(&ws.rw[pr.x], v);
+        if (s) atomicOr(&ws.st[qi], s);
+    }
+}
+
+// between rounds: the overflow list just written becomes the next round's
+// input list, and the pair list is emptied
+__global__ void k_next_round(Workspace ws) {
+    if (threadIdx.x == 0) {
+        ws.counters[5] = ws.counters[3];
+        ws.counters[6] += ws.counters[3];
+        ws.counters[7] += ws.counters[0];  // pairs of the finished round
+        ws.counters[3] = 0;
+        ws.counters[0] = 0;
+        ws.counters[2] = 0;
+    }
+}
+
+__global__ void k_accum(Workspace ws) {
+    if (threadIdx.x < 8) ws.acc[threadIdx.x] += (unsigned long long)ws.counters[threadIdx.x];
+}
+
+__global__ void k_rfinish(const int* rlist, Workspace ws, double* out_w, int* out_label, uint32_t* out_status) {
+    int cnt = ws.counters[1];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        int qi = rlist[k];
+        double w = ws.rw[k];
+        out_w[qi] = w;
+        if (out_label) out_label[qi] = (int)round(w);
+        if (out_status) out_status[qi] = ws.st[qi] | GWN_QS_REPAIRED;
+    }
+}
+
+}  // namespace gwn
+
+namespace gwn {
+
+// ---- Warp-cooperative FP64 repair traversal.  One warp per repaired point:
+// the warp keeps a node stack in shared memory and each step the lanes take up
+// to 32 nodes from its top, apply the far test in FP64 and push the children
+// of the nodes that fail it (positions by a warp prefix sum).  This spreads one
+// point's traversal over 32 lanes, which matters because FP64 issue is slow
+// and latency-bound when a single thread walks the tree.  Exact leaves: 2D in
+// place (FP64), 3D appended to the FP64 pair list (k_rpairs3).
+constexpr int kWarpStack = 2048;
+constexpr int kRepairWarps = 4;  // warps per block
+
+template <int DIM>
+__global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, const void* pts, int dtype, double beta2r,
+                                                                  const int* rlist, Workspace ws, double* out_w,
+                                                                  int* out_label, uint32_t* out_status) {
+    __shared__ int sstack[kRepairWarps][kWarpStack];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kRepairWarps + wid;
+    const int nw = gridDim.x * kRepairWarps;
+    const int cnt = ws.counters[1];
+    int* stk = sstack[wid];
+    for (int k = gw; k < cnt; k += nw) {
+        const int qi = rlist[k];
+        double q[3] = {0, 0, 0};
+        if (dtype == GWN_F32) {
+            const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * DIM;
+            for (int c = 0; c < DIM; ++c) q[c] = p[c];
+        } else {
+            const double* p = reinterpret_cast<const double*>(pts) + (size_t)qi * DIM;
+            for (int c = 0; c < DIM; ++c) q[c] = p[c];
+        }
+        double acc = 0.0;
+        uint32_t st = 0;
+        if (lane == 0) stk[0] = t.root;
+        int sp = 1;
+        __syncwarp();
+        while (sp > 0) {
+            const int take = min(sp, 32);
+            const int node = lane < take ? stk[sp - 1 - lane] : 0;
+            sp -= take;
+            __syncwarp();
+            int c0 = 0, c1 = 0, npush = 0;
+            if (lane < take) {
+                if (node < 0) {
+                    const int li = ~node;
+                    if (DIM == 2) {
+                        acc += leaf2_eval64(t, li, q[0], q[1], st);
+                    } else {
+                        const double* h = t.lhdr64 + (size_t)li * 4;
+                        double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
+                        if (beta2r > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2r * h[3]) {
+                            acc += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
+                        } else {
+                            int slot = atomicAdd(&ws.counters[4], 1);
+                            if (slot < kRepairPairCap) ws.rpairs[slot] = make_int2(k, li);
+                            else acc += leaf3_eval64(t, li, q[0], q[1], q[2], st);
+                        }
+                    }
+                } else {
+                    const double* h = t.hdr64 + (size_t)node * 4;
+                    double rx = h[0] - q[0], ry = h[1] - q[1], rz = DIM == 3 ? h[2] - q[2] : 0.0;
+                    double d2 = rx * rx + ry * ry + rz * rz;
+                    if (beta2r > 0 && d2 > beta2r * h[3]) {
+                        if (DIM == 2) acc += far2_eval<double>(t.mom64 + (size_t)node * kMom2F64, rx, ry);
+                        else acc += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz);
+                    } else {
+                        int2 ch = t.child[node];
+                        c0 = ch.x;
+                        c1 = ch.y;
+                        npush = 2;
+                    }
+                }
+            }
+            // warp prefix sum of the pushes
+            int incl = npush;
+            for (int off = 1; off < 32; off <<= 1) {
+                int v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (sp + total > kWarpStack) {
+                st |= GWN_QS_UNRESOLVED;  // stack full: those subtrees are dropped (flagged)
+            } else if (npush) {
+                stk[sp + incl - 2] = c1;
+                stk[sp + incl - 1] = c0;
+            }
+            if (sp + total <= kWarpStack) sp += total;
+            __syncwarp();
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            st |= __shfl_xor_sync(0xffffffffu, st, off);
+        }
+        if (lane == 0) {
+            if (DIM == 2) {
+                out_w[qi] = acc;
+                if (out_label) out_label[qi] = (int)round(acc);
+                if (out_status) out_status[qi] = ws.st[qi] | st | GWN_QS_REPAIRED;
+            } else {
+                ws.rw[k] = acc;
+                ws.st[qi] = st;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace gwn

@@ -89,7 +89,7 @@ def loops():
 
 def test_loops_fp32_repair_subset(loops, oracle_lib):
     curves, q, idx = loops
-    m = gwn.gwn_build_2d(curves, beta=12.0)
+    m = gwn.gwn_build_2d(curves, beta=16.0)
     w, lab, st = m.query(torch.from_numpy(q).float().cuda())
     w = w.cpu().numpy()
     st = st.cpu().numpy()
@@ -115,7 +115,7 @@ def test_edge_cases(oracle_lib):
         for n in (1, 7, 129, 1000):
             q = rng.uniform(-1.5, 3.5, size=(n, 2)).astype(np.float32).astype(np.float64)
             w_ref, _ = oracle_lib.gwn2d(curves, q)
-            w, lab, st = m.query(torch.from_numpy(q).cuda(), precision=gwn.PREC_FP64)
+            w, lab, st = m.query(torch.from_numpy(q).cuda(), precision=gwn.PREC_FP64, mode=gwn.MODE_DIRECT)
             assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-9
             w32, _, _ = m.query(torch.from_numpy(q).float().cuda())
             assert np.max(np.abs(w32.cpu().numpy() - w_ref)) <= 1e-4
@@ -125,3 +125,13 @@ def test_edge_cases(oracle_lib):
     m = gwn.gwn_build_2d(shapes[0])
     w, _, _ = m.query(torch.zeros((0, 2), device="cuda"))
     assert w.numel() == 0
+
+
+def test_autotuned_beta_2d(loops, oracle_lib):
+    curves, q, idx = loops
+    m = gwn.gwn_build_2d(curves, beta=0.0, tolerance=1e-4)
+    w, _, _ = m.query(torch.from_numpy(q).float().cuda())
+    w = w.cpu().numpy()[idx[:1500]]
+    w_ref, fl = oracle_lib.gwn2d(curves, q[idx[:1500]])
+    ok = np.isfinite(w_ref)
+    assert np.max(np.abs(w[ok] - w_ref[ok])) <= 1e-4

@@ -127,3 +127,18 @@ def test_cad_model_fp32_and_direct(oracle_lib):
     md = gwn.gwn_build_3d(patches, max_aabb_frac=0.0)
     wd, _, _ = md.query(_q(q[:600]), mode=gwn.MODE_DIRECT, precision=gwn.PREC_FP32)
     assert np.max(np.abs(wd.cpu().numpy()[ok] - w_ref[ok])) <= 1e-4
+
+
+def test_autotuned_beta_meets_tolerance(oracle_lib):
+    """beta = 0: the build picks (beta, beta_leaf) for max |dGWN| <= tolerance."""
+    patches, q = configs.cad_3d(4321, 600, 6000)
+    m = gwn.gwn_build_3d(patches, beta=0.0, tolerance=1e-4)
+    info = m.info()
+    assert info["beta"] >= 2.0 and 2.0 <= info["beta_leaf"] <= info["beta"]
+    rng = np.random.default_rng(6)
+    sel = rng.choice(q.shape[0], 400, replace=False)
+    w_ref, fl = oracle_lib.gwn3d(patches, q[sel], near_thr=1e-6 * _diag(patches))
+    w, _, _ = m.query(_q(q.astype(np.float32)))
+    w = w.cpu().numpy()[sel]
+    ok = np.isfinite(w_ref)
+    assert np.max(np.abs(w[ok] - w_ref[ok])) <= 1e-4

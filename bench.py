@@ -99,6 +99,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(ms, units_per_rank, world, device):
+    """Replicas: every rank processes units_per_rank in ms.  Returns the
+    slowest rank's ms and the whole-job rate (units of all ranks / that time)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1e3)
+
+
 def flops_traversal(w):
     # per internal node / leaf visited: far test (10); per Taylor evaluation: 72
     return 10 * (w["nodes"] + w["leaf_tests"]) + 72 * w["far"]
@@ -154,6 +166,82 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def serving_leg(gwn, phase_s: float, log_fn):
+    """Serving workload: 8 resident models behind the gwn_serve_* loop.
+
+    Phase 1 (saturation): the first requests of the trace, about phase_s seconds
+    of work, are submitted at once; sustained throughput = points / time to
+    drain.  Phase 2 (open loop): Poisson arrivals at half the saturated request
+    rate for phase_s seconds; p50/p99 of submit -> results ready.
+    """
+    import threading as th
+    from synth import configs
+
+    specs = configs.serve_models()
+    models = []
+    for dim, prims, lo, hi in specs:
+        models.append(gwn.gwn_build_2d(prims) if dim == 2 else gwn.gwn_build_3d(prims))
+    rng = np.random.default_rng(7)
+    pools = [configs.uniform_queries(lo, hi, 2_000_000, rng).astype(np.float32) for _, _, lo, hi in specs]
+    log_fn("serving: 8 models built")
+
+    def run(times, midx, sizes, open_loop):
+        srv = gwn.Server(n_slots=4)
+        ids = [srv.add_model(m) for m in models]
+        rids = []
+        done = th.Event()
+
+        def poller():
+            k = 0
+            while k < len(times):
+                while k >= len(rids):
+                    if done.wait(0.001) and k >= len(rids):
+                        return
+                srv.poll(rids[k][0], rids[k][1], timeout_ms=120000)
+                k += 1
+
+        pt = th.Thread(target=poller)
+        pt.start()
+        t0 = time.perf_counter()
+        for t, mi, n in zip(times, midx, sizes):
+            if open_loop:
+                dt = t - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            off = int(rng.integers(0, pools[mi].shape[0] - n + 1))
+            rids.append((srv.submit(ids[mi], pools[mi][off:off + n]), int(n)))
+        done.set()
+        pt.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return st, wall
+
+    t_all, m_all, n_all = configs.serve_trace(2000.0, 60.0)
+    # saturation: enough requests for about phase_s seconds at a first guess of 5e6 points/s
+    k = int(np.searchsorted(np.cumsum(n_all), 5e6 * phase_s)) + 1
+    st, wall = run(t_all[:k], m_all[:k], n_all[:k], open_loop=False)
+    sat_qps = st["points_completed"] / wall
+    sat_rps = k / wall
+    log_fn(f"serving: saturation {sat_qps:.3e} points/s, {sat_rps:.1f} req/s")
+    rate = 0.5 * sat_rps
+    t_o, m_o, n_o = configs.serve_trace(rate, phase_s, seed=configs.BASE_SEED + 7)
+    st2, wall2 = run(t_o, m_o, n_o, open_loop=True)
+    log_fn(f"serving: open loop {rate:.1f} req/s, p50 {st2['p50_ms']:.1f} ms, p99 {st2['p99_ms']:.1f} ms")
+    for m in models:
+        m.release()
+    return {"metric": "serving latency, submit -> results ready", "unit": "ms",
+            "models": "8 resident: 2 loops_2d (19,000 curves), 2 sphere_3d (384 patches), "
+                      "4 cad_3d (1.5k-17k patches)",
+            "sizes": "log-normal, median 16,384 points, sigma 1.5, clamped to [1000, 2e6]",
+            "saturation": {"requests": k, "points_per_s": sat_qps, "requests_per_s": sat_rps},
+            "open_loop": {"rate_req_s": rate, "load": 0.5, "duration_s": phase_s,
+                          "requests": int(st2["completed"]), "p50_ms": st2["p50_ms"],
+                          "p99_ms": st2["p99_ms"], "mean_ms": st2["mean_ms"],
+                          "points_per_s": st2["points_completed"] / wall2},
+            "slots": 4, "precision": "fp32 bulk + fp64 repair"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,6 +252,9 @@ def main():
     ap.add_argument("--models", type=int, default=16, help="first K models of the workload (default all 16)")
     ap.add_argument("--query-scale", type=float, default=1.0, help="fraction of each model's queries (default 1)")
     ap.add_argument("--beta", type=float, default=BETA)
+    ap.add_argument("--beta-leaf", type=float, default=0.0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving phase")
     ap.add_argument("--kernels-only", action="store_true",
                     help="timed steps only (no e2e, direct-sum or CPU legs); for profiler runs")
     args = ap.parse_args()
@@ -188,7 +279,7 @@ def main():
     log("workload generated")
     models, points, outs = [], [], []
     for patches, q in workload:
-        m = gwn.gwn_build_3d(patches, beta=args.beta)
+        m = gwn.gwn_build_3d(patches, beta=args.beta, beta_leaf=args.beta_leaf)
         models.append(m)
         pt = torch.from_numpy(q.astype(np.float32)).to(dev)
         points.append(pt)
@@ -222,21 +313,19 @@ def main():
         dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps' launches
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clocks = clk.stop()
     log(f"timed {args.steps} steps: {ms:.1f} ms/step")
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * total_q / (ms / 1e3)
+    ms, value = aggregate_ranks(ms, total_q, world, dev)
 
     if args.kernels_only:
         if rank == 0:
@@ -246,7 +335,7 @@ def main():
 
     # kernel-level numbers (untimed passes): event timing of the traversal and
     # exact-leaf kernels on the query stream, and the algorithmic work counters
-    trav_us, leaf_us, fl_trav, fl_leaf, repaired, pairs = 0.0, 0.0, 0.0, 0.0, 0, 0
+    trav_us, leaf_us, fl_trav, fl_leaf, repaired, pairs, near = 0.0, 0.0, 0.0, 0.0, 0, 0, 0
     for m, p, o in zip(models, points, outs):
         m.query(p, out=o, stream=stream, profile=True)
         s = m.last_query_stats()
@@ -258,6 +347,7 @@ def main():
         fl_leaf += flops_leaves(w)
         repaired += w["repaired"]
         pairs += w["pairs"]
+        near += w["near_band"]
     log("profiled and counted")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clocks.get("sm_mhz") or 2070.0
@@ -319,6 +409,10 @@ def main():
         cpu = {"value": nq / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
                "sample": f"{ORACLE_SAMPLE} queries of each of the 16 models (exact FP64 direct sum), {dt:.1f} s"}
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = serving_leg(gwn, args.serve_seconds, log)
+
     # kernels per chunk of up to 2^19 points: bin, scan, scatter; 3 rounds of traversal, pair key, scan,
     # pair scatter, pair eval, near band (+ round switch x2); overflow, finish, repair x3, counter accumulate
     launches_per_step = sum(29 * math.ceil(p.shape[0] / (1 << 19)) for p in points)
@@ -340,10 +434,13 @@ def main():
         "direct_sum": {"value": direct_qps, "unit": "queries/s",
                        "sample": f"{DIRECT_SAMPLE} queries per model, FP32, per-query time extrapolated",
                        "speedup": value / direct_qps},
-        "work": {"pairs_per_query": pairs / total_q, "repaired_fraction": repaired / total_q},
+        "work": {"pairs_per_query": pairs / total_q, "near_band_pairs_per_query": near / total_q,
+                 "repaired_fraction": repaired / total_q},
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
     }
+    if serving is not None:
+        line["serving"] = serving
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

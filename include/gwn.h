@@ -202,6 +202,60 @@ gwn_status gwn_model_leaves(gwn_model model, int64_t* prim, double* param);
  * Any pointer may be NULL. */
 gwn_status gwn_model_tree(gwn_model model, int32_t* child, double* x0, double* r, double* mom);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop over device-resident models with continuous batching (the
+ * paper has no serving layer; this runs Algorithm 1's batched query per
+ * request).  Requests are queued by gwn_serve_submit and admitted in arrival
+ * order by a worker thread whenever one of n_slots slots (a CUDA stream with
+ * its own query workspace) is free and the request's device memory (points +
+ * outputs) fits the budget; requests in different slots run concurrently on
+ * the GPU.  Models must outlive the server and are not released by it. */
+typedef struct gwn_server_s* gwn_server;
+
+typedef struct {
+    int64_t mem_budget_bytes; /* device memory for the buffers (points + outputs) of the requests in
+                                 flight (default 40 GiB); the slots' query workspaces, one per slot
+                                 sized for the largest model, come on top */
+    int32_t n_slots;          /* requests in flight at once (default 4) */
+    int32_t device;           /* -1 = current */
+} gwn_serve_opts;
+
+void gwn_default_serve_opts(gwn_serve_opts* opts);
+
+/* Start a server (spawns its worker thread).  Errors: INVALID_ARG, OOM. */
+gwn_status gwn_serve_create(const gwn_serve_opts* opts, gwn_server* out);
+
+/* Register a model; *model_id receives its id.  Only while no request is in
+ * flight (else GWN_ERR_BUSY). */
+gwn_status gwn_serve_add_model(gwn_server server, gwn_model model, int32_t* model_id);
+
+/* Queue a request: n host points (n x dim, dtype GWN_F32 or GWN_F64), copied
+ * before the call returns.  *request_id identifies it.  Errors: NOT_FOUND
+ * (model id), INVALID_ARG (empty, or larger than the memory budget). */
+gwn_status gwn_serve_submit(gwn_server server, int32_t model_id, const void* points, int32_t dtype, size_t n,
+                            uint64_t* request_id);
+
+/* Wait up to timeout_ms for a request; on success copy its n values
+ * (out_w, FP64) and labels (out_label, nullable) and forget the request.
+ * GWN_ERR_TIMEOUT if it has not finished (it stays queued); NOT_FOUND for an
+ * unknown or already collected id. */
+gwn_status gwn_serve_poll(gwn_server server, uint64_t request_id, double* out_w, int32_t* out_label,
+                          int32_t timeout_ms);
+
+typedef struct {
+    int64_t submitted, completed, in_flight, queued;
+    int64_t points_completed;
+    double p50_ms, p99_ms, mean_ms;  /* submit -> results ready, over completed requests */
+    double queries_per_s;            /* points completed / (last completion - first submit) */
+    int64_t budget_used_bytes;
+} gwn_server_stats;
+
+gwn_status gwn_serve_stats(gwn_server server, gwn_server_stats* stats);
+
+/* Finish the requests already admitted or queued, stop the worker and free
+ * the server's memory.  NULL is a no-op. */
+gwn_status gwn_serve_destroy(gwn_server server);
+
 /* Release a model and all its device memory.  NULL is a no-op. */
 gwn_status gwn_release(gwn_model model);
 

@@ -64,6 +64,17 @@ class gwn_model_stats(ctypes.Structure):
                 ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double)]
 
 
+class gwn_serve_opts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("n_slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class gwn_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("points_completed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("queries_per_s", ctypes.c_double),
+                ("budget_used_bytes", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "gwn_default_build_opts": (None, [ctypes.POINTER(gwn_build_opts)]),
@@ -77,6 +88,14 @@ _SIGS = {
     "gwn_model_leaves": (ctypes.c_int, [_P, _P, _P]),
     "gwn_model_tree": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gwn_release": (ctypes.c_int, [_P]),
+    "gwn_default_serve_opts": (None, [ctypes.POINTER(gwn_serve_opts)]),
+    "gwn_serve_create": (ctypes.c_int, [ctypes.POINTER(gwn_serve_opts), ctypes.POINTER(_P)]),
+    "gwn_serve_add_model": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "gwn_serve_submit": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_size_t,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "gwn_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32]),
+    "gwn_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(gwn_server_stats)]),
+    "gwn_serve_destroy": (ctypes.c_int, [_P]),
     "gwn_last_error": (ctypes.c_char_p, []),
     "gwn_version": (ctypes.c_char_p, []),
 }
@@ -328,3 +347,56 @@ def gwn_release(model: Model):
 
 def gwn_version() -> str:
     return lib().gwn_version().decode()
+
+
+class Server:
+    """The gwn_serve_* request loop (continuous batching over resident models)."""
+
+    def __init__(self, mem_budget_bytes: int = 40 << 30, n_slots: int = 4, device: int = -1):
+        o = gwn_serve_opts()
+        lib().gwn_default_serve_opts(ctypes.byref(o))
+        o.mem_budget_bytes, o.n_slots, o.device = int(mem_budget_bytes), int(n_slots), int(device)
+        h = ctypes.c_void_p()
+        _check(lib().gwn_serve_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+        self.models = []
+        self.dims = []
+
+    def add_model(self, model: Model) -> int:
+        mid = ctypes.c_int32()
+        _check(lib().gwn_serve_add_model(self.handle, model.handle, ctypes.byref(mid)))
+        self.models.append(model)
+        self.dims.append(model.dim)
+        return mid.value
+
+    def submit(self, model_id: int, points) -> int:
+        pts = np.ascontiguousarray(points)
+        if pts.dtype not in (np.float32, np.float64):
+            pts = pts.astype(np.float64)
+        rid = ctypes.c_uint64()
+        _check(lib().gwn_serve_submit(self.handle, int(model_id), pts.ctypes.data,
+                                      F32 if pts.dtype == np.float32 else F64, pts.shape[0], ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, request_id: int, n: int, timeout_ms: int = 60000):
+        w = np.zeros(n)
+        lab = np.zeros(n, dtype=np.int32)
+        _check(lib().gwn_serve_poll(self.handle, ctypes.c_uint64(request_id), w.ctypes.data, lab.ctypes.data,
+                                    int(timeout_ms)))
+        return w, lab
+
+    def stats(self) -> dict:
+        s = gwn_server_stats()
+        _check(lib().gwn_serve_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gwn_serve_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -29,6 +29,7 @@
 #include "kernels2d.cuh"
 #include "kernels3d.cuh"
 #include "query_pipeline.cuh"
+#include "model.h"
 
 using namespace gwn;
 
@@ -62,30 +63,7 @@ struct DeviceGuard {
 };
 }  // namespace
 
-struct gwn_model_s {
-    int dim = 2;
-    int leaf_far = 0;
-    int device = 0;
-    int64_t n_primitives = 0;
-    gwn_build_opts opts{};
-    double build_ms = 0;
-    HostModel host;       // host copy (inspection)
-    DevTree tree{};
-    std::vector<void*> allocs;
-    size_t device_bytes = 0;
-    // scratch owned by the model: query workspace and host staging
-    std::mutex mu;
-    void* ws_mem = nullptr;
-    size_t ws_bytes = 0;
-    size_t ws_n = 0;
-    Workspace ws{};
-    static constexpr int kMaxProfChunks = 32;
-    cudaEvent_t ev[kMaxProfChunks][4] = {};
-    int prof_chunks = 0;
-    bool profiled = false;
-    void* stage = nullptr;
-    size_t stage_cap = 0;
-};
+
 
 namespace {
 
@@ -365,9 +343,11 @@ __global__ void __launch_bounds__(128) k_repair(DevTree t, const void* pts, int 
 }
 
 // Bytes of the query workspace for n points of model m, and its layout.
+// dim 0 lays out a workspace that serves both 2D and 3D models.
 size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* ws) {
-    const long long cap = dim == 3 ? (long long)n * 96 + 65536 : 0;
-    const size_t cells = (size_t)1 << (dim == 2 ? 2 * kBinBits2 : 3 * kBinBits3);
+    const long long cap = dim != 2 ? (long long)n * 96 + 65536 : 0;
+    const size_t cells2 = (size_t)1 << (2 * kBinBits2), cells3 = (size_t)1 << (3 * kBinBits3);
+    const size_t cells = dim == 2 ? cells2 : dim == 3 ? cells3 : std::max(cells2, cells3);
     const size_t hist = std::max(cells, (size_t)n_leaves) + 1;
     const size_t keyn = std::max((size_t)n, (size_t)cap);
     size_t off = 0;
@@ -384,15 +364,15 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     w.st = (uint32_t*)carve(n * sizeof(uint32_t));
     w.pairs = (int2*)carve((size_t)cap * sizeof(int2));
     w.pairs2 = (int2*)carve((size_t)cap * sizeof(int2));
-    w.counters = (int*)carve(8 * sizeof(int));
-    w.rpairs = (int2*)carve((dim == 3 ? (size_t)kRepairPairCap : 0) * sizeof(int2));
+    w.counters = (int*)carve(kCounterCount * sizeof(int));
+    w.rpairs = (int2*)carve((dim != 2 ? (size_t)kRepairPairCap : 0) * sizeof(int2));
     w.rw = (double*)carve(n * sizeof(double));
-    w.pairs64 = (int2*)carve((dim == 3 ? n : 0) * sizeof(int2));
+    w.pairs64 = (int2*)carve((dim != 2 ? n : 0) * sizeof(int2));
     w.rlist = (int*)carve(n * sizeof(int));
-    w.olist = (int*)carve((dim == 3 ? n : 0) * sizeof(int));
-    w.olist2 = (int*)carve((dim == 3 ? n : 0) * sizeof(int));
+    w.olist = (int*)carve((dim != 2 ? n : 0) * sizeof(int));
+    w.olist2 = (int*)carve((dim != 2 ? n : 0) * sizeof(int));
     w.work = (unsigned long long*)carve(kWorkCount * sizeof(unsigned long long));
-    w.acc = (unsigned long long*)carve(8 * sizeof(unsigned long long));
+    w.acc = (unsigned long long*)carve(kCounterCount * sizeof(unsigned long long));
     w.pair_cap = cap;
     if (ws) *ws = w;
     return off;
@@ -473,7 +453,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         return GWN_OK;
     }
     int* rcount = ws.counters + 1;
-    GWN_CUDA_TRY(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(int), st));
+    GWN_CUDA_TRY(cudaMemsetAsync(ws.counters, 0, kCounterCount * sizeof(int), st));
     if (p.mode == GWN_MODE_DIRECT) {
         if (m->dim == 2)
             k_query32<2><<<nb, B, 0, st>>>(m->tree, pts, dtype, (long long)n, p, out_w, out_label, out_status, ws.rlist, rcount);
@@ -545,7 +525,10 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         unsigned rb = (unsigned)std::min<long long>(std::max<long long>(nb, sms * 4), (long long)sms * 8);
         if (rb == 0) rb = 1;
         const unsigned wb = (unsigned)(sms * 4);  // blocks of kRepairWarps warps, one warp per repaired point
-        if (p.mode == GWN_MODE_DIRECT || !(p.beta2_repair > 0)) {
+        // 3D with beta_repair = 0 (exact sum over every leaf) still goes through the
+        // warp traversal: every leaf becomes an FP64 pair, and the pairs of all
+        // repaired points spread over the whole GPU instead of one warp per point
+        if (p.mode == GWN_MODE_DIRECT || (m->dim == 2 && !(p.beta2_repair > 0))) {
             if (m->dim == 2) k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
             else k_repair<3><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
         } else if (m->dim == 2) {
@@ -569,7 +552,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
 gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
                               uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const Workspace& ws) {
     const size_t esz = (dtype == GWN_F32 ? sizeof(float) : sizeof(double)) * m->dim;
-    GWN_CUDA_TRY(cudaMemsetAsync(ws.acc, 0, 8 * sizeof(unsigned long long), st));
+    GWN_CUDA_TRY(cudaMemsetAsync(ws.acc, 0, kCounterCount * sizeof(unsigned long long), st));
     if (qo.count_work) GWN_CUDA_TRY(cudaMemsetAsync(ws.work, 0, kWorkCount * sizeof(unsigned long long), st));
     m->prof_chunks = 0;
     m->profiled = qo.profile != 0;
@@ -672,8 +655,9 @@ static gwn_status autotune(gwn_model_s* m) {
     qo.mode = GWN_MODE_DIRECT;
     qo.precision = GWN_PREC_FP64;
     if (s == GWN_OK) s = gwn_enqueue_device(m, dp, GWN_F32, nv, ref, nullptr, nullptr, qo, 0, m->ws);
-    const double betas[] = {2.0, 3.0, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0};
-    const double leafb[] = {2.0, 2.5, 3.0, 4.0, 6.0, 0.0};
+    const double betas[] = {3.0, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0};
+    // 2D leaves have no separate factor (0 = beta); 3D leaves: per-level factors
+    const double leafb[] = {0.0, 2.0, 2.5, 3.0, 4.0, 5.0};
     double best_cost = 1e300, best_b = 0, best_bl = 0;
     double fb_err = 1e300, fb_b = 0, fb_bl = 0;  // fallback: smallest error seen
     const double tol = 0.5 * m->opts.tolerance;
@@ -682,6 +666,7 @@ static gwn_status autotune(gwn_model_s* m) {
         for (double bl : leafb) {
             if (s != GWN_OK) break;
             if (d == 2 && bl != 0.0) continue;
+            if (d == 3 && bl == 0.0) continue;
             if (bl > b) continue;
             double blv = bl == 0.0 ? b : bl;
             gwn_query_opts q2;
@@ -695,7 +680,7 @@ static gwn_status autotune(gwn_model_s* m) {
             cudaMemset(err, 0, sizeof(double));
             k_err<<<4, 128>>>(nv, ref, w, err);
             double e = 0;
-            unsigned long long wk[kWorkCount] = {}, acc[8] = {};
+            unsigned long long wk[kWorkCount] = {}, acc[kCounterCount] = {};
             if (cudaMemcpy(&e, err, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
                 cudaMemcpy(wk, m->ws.work, sizeof(wk), cudaMemcpyDeviceToHost) != cudaSuccess ||
                 cudaMemcpy(acc, m->ws.acc, sizeof(acc), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -846,11 +831,12 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     return GWN_OK;
 }
 
+
 gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
     if (!m || !out) return fail(GWN_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard g(m->device);
     std::lock_guard<std::mutex> lk(m->mu);
-    unsigned long long c[8] = {};
+    unsigned long long c[kCounterCount] = {};
     unsigned long long wk[kWorkCount] = {};
     if (m->ws_mem) {
         GWN_CUDA_TRY(cudaDeviceSynchronize());
@@ -860,6 +846,7 @@ gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
     for (int k = 0; k < 16; ++k) out[k] = 0;
     for (int k = 0; k < 4; ++k) out[k] = (int64_t)c[k];
     out[0] = (int64_t)(c[0] + c[7]);  // pairs over all rounds
+    out[2] = (int64_t)(c[2] + c[8]);  // near-band (FP64) pairs over all rounds
     out[3] = (int64_t)(c[6] + c[3]);  // points whose pairs overflowed in any round
     for (int k = 0; k < kWorkCount; ++k) out[4 + k] = (int64_t)wk[k];
     if (m->profiled) {
@@ -938,3 +925,11 @@ const char* gwn_last_error(void) { return g_err.c_str(); }
 const char* gwn_version(void) { return "gwn-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+gwn_status gwn_fail(gwn_status s, const std::string& msg) { return fail(s, msg); }
+
+size_t gwn_workspace_bytes(int dim, int n_leaves, char* base, gwn::Workspace* ws) {
+    return workspace_layout(dim, n_leaves, kChunk, base, ws);
+}
+
+size_t gwn_chunk_points() { return kChunk; }

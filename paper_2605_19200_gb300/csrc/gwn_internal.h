@@ -138,4 +138,31 @@ struct QueryParams {
     int precision;             // GWN_PREC_*
 };
 
+constexpr long long kRepairPairCap = 1ll << 22;  // FP64 repair pairs per chunk
+constexpr int kCounterCount = 16;                // device counters of one chunk
+
+// Scratch of one in-flight query (one chunk of points), carved from one
+// device allocation (see workspace_layout in gwn_api.cu).
+struct Workspace {
+    int2* pairs64;    // near-band pairs (capacity n)
+    int2* rpairs;     // FP64 repair pairs (kRepairPairCap, 3D)
+    double* rw;       // FP64 repair accumulators (n)
+    int* perm;        // n
+    int* key;         // max(n, pair capacity)
+    int* hist;        // max(cells, n_leaves) + 1
+    float* wacc;      // n
+    uint32_t* st;     // n
+    int2* pairs;      // pair capacity
+    int2* pairs2;     // pair capacity (sorted)
+    int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
+                      // [5] overflowed points of the current round (list input), [6] total overflow,
+                      // [7] pairs of finished rounds, [8] near-band pairs of finished rounds
+    int* olist;       // n: points whose pairs did not fit (rounds alternate with olist2)
+    int* olist2;      // n
+    unsigned long long* work;  // kWorkCount counters
+    unsigned long long* acc;   // per-query totals of the counters over all chunks
+    int* rlist;       // n
+    long long pair_cap;
+};
+
 }  // namespace gwn

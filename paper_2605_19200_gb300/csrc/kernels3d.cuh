@@ -288,18 +288,27 @@ GWN_HD int leaf_hit(const DevTree& t, const Leaf3Info& I, const G& g, const T q[
         e2[1] = nrm[2] * e1[0] - nrm[0] * e1[2];
         e2[2] = nrm[0] * e1[1] - nrm[1] * e1[0];
     }
-    // quick reject: q's projection outside the projected control-net box
-    T mn1 = T(1e30), mx1 = T(-1e30), mn2 = T(1e30), mx2 = T(-1e30);
+    // quick rejects from the convex hull of the control points (positive
+    // weights): q's projection outside the projected control-net box, or the
+    // whole net behind q along the half line (every hull point has a height
+    // sig n . (P - q) below -tau_eps, so no crossing exists and q is not near
+    // the leaf's surface either)
+    const T tau_eps = sizeof(T) == 4 ? T(1e-4) * diag : T(1e-12) * diag;
+    T mn1 = T(1e30), mx1 = T(-1e30), mn2 = T(1e30), mx2 = T(-1e30), mxh = T(-1e30);
     for (int k = 0; k < 16; ++k) {
         T h[4];
         g.net_pt(k, h);
         T iw = T(1) / h[3];
-        T p1 = (h[0] * iw - q[0]) * e1[0] + (h[1] * iw - q[1]) * e1[1] + (h[2] * iw - q[2]) * e1[2];
-        T p2 = (h[0] * iw - q[0]) * e2[0] + (h[1] * iw - q[1]) * e2[1] + (h[2] * iw - q[2]) * e2[2];
+        T d0 = h[0] * iw - q[0], d1 = h[1] * iw - q[1], d2 = h[2] * iw - q[2];
+        T p1 = d0 * e1[0] + d1 * e1[1] + d2 * e1[2];
+        T p2 = d0 * e2[0] + d1 * e2[1] + d2 * e2[2];
+        T ph = sig * (d0 * nrm[0] + d1 * nrm[1] + d2 * nrm[2]);
         mn1 = fmin(mn1, p1); mx1 = fmax(mx1, p1);
         mn2 = fmin(mn2, p2); mx2 = fmax(mx2, p2);
+        mxh = fmax(mxh, ph);
     }
     if (mn1 > 0 || mx1 < 0 || mn2 > 0 || mx2 < 0) return kHitNone;
+    if (mxh < -tau_eps) return kHitNone;
     // exact test: winding number of the projected domain boundary (the net's
     // four edge curves, rational cubics) around q's projection.  Zero means the
     // line along the normal misses the leaf's rectangle altogether.
@@ -354,7 +363,6 @@ GWN_HD int leaf_hit(const DevTree& t, const Leaf3Info& I, const G& g, const T q[
     if (u < -eps || u > T(1) + eps || v < -eps || v > T(1) + eps) return kHitNone;
     net_eval3<T>(g, u, v, S, Su, Sv);
     T tau = sig * (nrm[0] * (S[0] - q[0]) + nrm[1] * (S[1] - q[1]) + nrm[2] * (S[2] - q[2]));
-    T tau_eps = sizeof(T) == 4 ? T(1e-4) * diag : T(1e-12) * diag;
     if (fabs(tau) < tau_eps) return kHitUnsure;  // q too close to the surface to decide here
     if (u < eps || u > T(1) - eps || v < eps || v > T(1) - eps) return kHitUnsure;  // on the leaf's rectangle edge
     if (tau < 0) return kHitNone;

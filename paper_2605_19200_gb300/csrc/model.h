@@ -1,0 +1,52 @@
+// model.h -- the model object behind gwn_model and the host functions the
+// serving loop shares with the query entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gwn.h"
+#include "build.h"
+#include "gwn_internal.h"
+
+struct gwn_model_s {
+    int dim = 2;
+    int leaf_far = 0;
+    int device = 0;
+    int64_t n_primitives = 0;
+    gwn_build_opts opts{};
+    double build_ms = 0;
+    gwn::HostModel host;       // host copy (inspection)
+    gwn::DevTree tree{};
+    std::vector<void*> allocs;
+    size_t device_bytes = 0;
+    // scratch owned by the model: query workspace and host staging
+    std::mutex mu;
+    void* ws_mem = nullptr;
+    size_t ws_bytes = 0;
+    size_t ws_n = 0;
+    gwn::Workspace ws{};
+    static constexpr int kMaxProfChunks = 32;
+    cudaEvent_t ev[kMaxProfChunks][4] = {};
+    int prof_chunks = 0;
+    bool profiled = false;
+    void* stage = nullptr;
+    size_t stage_cap = 0;
+};
+
+// Record an error message for gwn_last_error() and return the status.
+gwn_status gwn_fail(gwn_status s, const std::string& msg);
+
+// Enqueue a query (device-resident points and outputs) on `st` using workspace `ws`.
+gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
+                              uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const gwn::Workspace& ws);
+
+// Bytes of a query workspace for `dim` (0 = either dimension) and `n_leaves`;
+// when base != nullptr also lays it out in the allocation at base.
+size_t gwn_workspace_bytes(int dim, int n_leaves, char* base, gwn::Workspace* ws);
+
+// Points one workspace (one chunk of a query) holds.
+size_t gwn_chunk_points();

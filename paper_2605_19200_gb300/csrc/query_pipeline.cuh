@@ -25,33 +25,11 @@
 namespace gwn {
 
 constexpr int kBinBits2 = 9;   // 512 x 512 cells in 2D
-constexpr int kBinBits3 = 6;   // 64^3 cells in 3D
+constexpr int kBinBits3 = 5;   // 32^3 cells in 3D
 constexpr int kPairLocal = 8;  // pairs a thread buffers before reserving space
 constexpr uint32_t kPairOverflow = 0x100u;  // internal status bit: the point's pairs did not fit
 
-constexpr long long kRepairPairCap = 1ll << 22;  // FP64 repair pairs per chunk
 
-struct Workspace {
-    int2* pairs64;    // near-band pairs (capacity n)
-    int2* rpairs;     // FP64 repair pairs (kRepairPairCap, 3D)
-    double* rw;       // FP64 repair accumulators (n)
-    int* perm;        // n
-    int* key;         // max(n, pair capacity)
-    int* hist;        // max(cells, n_leaves) + 1
-    float* wacc;      // n
-    uint32_t* st;     // n
-    int2* pairs;      // pair capacity
-    int2* pairs2;     // pair capacity (sorted)
-    int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
-                      // [5] overflowed points of the current round (list input), [6] total overflow,
-                      // [7] pairs of finished rounds
-    int* olist;       // n: points whose pairs did not fit (rounds alternate with olist2)
-    int* olist2;      // n
-    unsigned long long* work;  // kWorkCount counters
-    unsigned long long* acc;   // per-query totals of counters[0..7] over all chunks
-    int* rlist;       // n
-    long long pair_cap;
-};
 
 __device__ __forceinline__ uint32_t spread_bits2(uint32_t x) {
     x &= 0x0000ffffu;
@@ -425,6 +403,7 @@ __global__ void k_next_round(Workspace ws) {
         ws.counters[5] = ws.counters[3];
         ws.counters[6] += ws.counters[3];
         ws.counters[7] += ws.counters[0];  // pairs of the finished round
+        ws.counters[8] += ws.counters[2];  // near-band pairs of the finished round
         ws.counters[3] = 0;
         ws.counters[0] = 0;
         ws.counters[2] = 0;
@@ -432,7 +411,7 @@ __global__ void k_next_round(Workspace ws) {
 }
 
 __global__ void k_accum(Workspace ws) {
-    if (threadIdx.x < 8) ws.acc[threadIdx.x] += (unsigned long long)ws.counters[threadIdx.x];
+    if (threadIdx.x < kCounterCount) ws.acc[threadIdx.x] += (unsigned long long)ws.counters[threadIdx.x];
 }
 
 __global__ void k_rfinish(const int* rlist, Workspace ws, double* out_w, int* out_label, uint32_t* out_status) {

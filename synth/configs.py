@@ -26,6 +26,11 @@ Workloads
                    outer polygonal trim loop and 0-2 polygonal holes each.
 * ``cad_batch_3d`` 16 ``cad_3d`` models, N log-uniform in [1000, 40000],
                    queries per model log-uniform in [65,536, 4,194,304].
+* ``serve_models`` / ``serve_trace``  8 resident models (2 ``loops_2d``-type,
+                   2 ``sphere_3d``-type, 4 ``cad_3d``-type) and an open-loop
+                   request trace: Poisson arrivals, sizes log-normal with median
+                   16,384 points and sigma 1.5 clamped to [1,000, 2,000,000],
+                   model chosen uniformly; points uniform in the model's box.
 """
 from __future__ import annotations
 
@@ -405,3 +410,36 @@ def cad_batch_3d(seed: int = BASE_SEED + 4, n_models: int = 16, query_scale: flo
         nq = max(64, int(spec.n_queries * query_scale))
         out.append(cad_3d(spec.seed, npch, nq))
     return out
+
+
+# ------------------------------------------------------------------ serving workload
+
+
+def serve_models(seed: int = BASE_SEED + 5, cad_patches: Tuple[int, ...] = (1500, 4000, 9000, 17000)):
+    """The 8 resident models of the serving workload: list of (dim, primitives, box lo, box hi)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(2):
+        curves, _ = loops_2d(seed=int(rng.integers(1 << 30)), res=2)
+        lo, hi = _bbox(np.concatenate([c.ctrl for c in curves]))
+        out.append((2, curves, lo, hi))
+    for k in range(2):
+        patches, _ = sphere_3d(seed=int(rng.integers(1 << 30)), n_queries=1)
+        lo, hi = _bbox(np.concatenate([p.ctrl.reshape(-1, 3) for p in patches]))
+        out.append((3, patches, lo, hi))
+    for npch in cad_patches:
+        patches, _ = cad_3d(int(rng.integers(1 << 30)), npch)
+        lo, hi = _bbox(np.concatenate([p.ctrl.reshape(-1, 3) for p in patches]))
+        out.append((3, patches, lo, hi))
+    return out
+
+
+def serve_trace(rate_per_s: float, duration_s: float, n_models: int = 8, seed: int = BASE_SEED + 6,
+                median: int = 16384, sigma: float = 1.5, lo: int = 1000, hi: int = 2000000):
+    """Open-loop request trace: arrays (arrival time s, model index, n points)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.poisson(rate_per_s * duration_s))
+    t = np.sort(rng.uniform(0.0, duration_s, n))
+    model = rng.integers(0, n_models, n)
+    size = np.clip(np.exp(rng.normal(math.log(median), sigma, n)), lo, hi).astype(np.int64)
+    return t, model, size

@@ -159,6 +159,35 @@ gwn_status gwn_query(gwn_model model, const void* points, int32_t points_dtype, 
                      double* out_w, int32_t* out_label, uint32_t* out_status, const gwn_query_opts* qopts,
                      void* stream);
 
+/* Query without any device allocation (the paper has no counterpart; this is
+ * an interface for callers that cannot allocate).
+ *
+ * gwn_query may call cudaMalloc: the first query on a model, and any query
+ * larger than the model's workspace, grow the workspace.  Some callers cannot
+ * allow that: real-time loops that must never stall on an allocation
+ * (cudaMalloc can synchronise the whole device), programs whose device memory
+ * is entirely owned by another allocator or a fixed budget decided at start-up,
+ * and code that must not change the process's device footprint after set-up.
+ * gwn_query_noalloc serves them: it runs the FP32
+ * traversal (every leaf evaluated in place, no spatial binning) and the FP64
+ * repair of GWN_PREC_FP32_REPAIR with the model's beta, and its only scratch
+ * is a file-scope device array of 4 MiB + 256 B that every GPU which loads
+ * the library keeps until the process exits.  It calls no cudaMalloc or
+ * cudaFree and no allocating library routine.
+ *   points, out_w, out_label, out_status: device pointers as in gwn_query
+ *     with GWN_MEM_DEVICE (out_label, out_status nullable); the call is
+ *     asynchronous on `stream`.
+ *   n <= 1,048,576 per call; larger n fails with GWN_ERR_INVALID_ARG.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Every call shares the one array: calls whose work overlaps on the GPU
+ *   (concurrent streams, or threads that do not serialise their streams)
+ *   race and must not be issued.
+ *   The model itself must have been built beforehand (gwn_build_* allocates). */
+gwn_status gwn_query_noalloc(gwn_model model, const void* points, int32_t points_dtype, size_t n, double* out_w,
+                             int32_t* out_label, uint32_t* out_status, void* stream);
+
 typedef struct {
     int32_t dim;
     int64_t n_primitives;   /* curves or patches given to the build */

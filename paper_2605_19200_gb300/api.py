@@ -84,6 +84,7 @@ _SIGS = {
     "gwn_query": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_size_t, _P, _P, _P,
                                  ctypes.POINTER(gwn_query_opts), _P]),
     "gwn_model_info": (ctypes.c_int, [_P, ctypes.POINTER(gwn_model_stats)]),
+    "gwn_query_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_size_t, _P, _P, _P, _P]),
     "gwn_last_query_stats": (ctypes.c_int, [_P, _P]),
     "gwn_model_leaves": (ctypes.c_int, [_P, _P, _P]),
     "gwn_model_tree": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -347,6 +348,18 @@ def gwn_release(model: Model):
 
 def gwn_version() -> str:
     return lib().gwn_version().decode()
+
+
+def gwn_query_noalloc(model: Model, points, out, stream=None):
+    """Query through gwn_query_noalloc: `points` a CUDA tensor (n x dim, float32
+    or float64), `out` = (w float64, label int32 or None, status int32 or
+    None) CUDA tensors supplied by the caller; the library allocates nothing."""
+    w, lab, st = out
+    dt = F32 if str(points.dtype).endswith("float32") else F64
+    _check(lib().gwn_query_noalloc(model.handle, points.data_ptr(), dt, points.shape[0], w.data_ptr(),
+                                   lab.data_ptr() if lab is not None else None,
+                                   st.data_ptr() if st is not None else None, _stream_handle(stream)))
+    return w, lab, st
 
 
 class Server:

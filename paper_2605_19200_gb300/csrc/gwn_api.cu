@@ -831,6 +831,110 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     return GWN_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------- query without allocation
+//
+// gwn_query_noalloc runs the FP32 traversal with FP64 repair without asking the
+// CUDA runtime for memory: its only scratch -- the list of points to repair
+// and its counter -- is the file-scope device array below, which every GPU
+// that loads this library holds until the process exits.  Host code cannot
+// use g_noalloc_scratch's name as a device address; the address comes from
+// cudaGetSymbolAddress, once per device, on the first call made with that
+// device current.
+
+static constexpr size_t kNoAllocMaxPoints = (size_t)1 << 20;   // points per call
+static constexpr int kNoAllocHeader = 64;                      // counter, padded to 256 bytes
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocHeader + kNoAllocMaxPoints];
+
+namespace {
+std::mutex g_noalloc_mu;
+int* g_noalloc_addr[256] = {};
+
+gwn_status noalloc_scratch(int dev, int** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (dev < 0 || dev >= 256) return fail(GWN_ERR_INVALID_ARG, "device ordinal out of range");
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(GWN_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = reinterpret_cast<int*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return GWN_OK;
+}
+
+// one thread per point: Algorithm 1 in FP32 with every leaf evaluated in place;
+// points near a half-integer or flagged go to the repair list
+template <int DIM>
+__global__ void __launch_bounds__(128) k_query_noalloc(DevTree t, const void* pts, int dtype, long long n, QueryParams p,
+                                                       double* out_w, int* out_label, uint32_t* out_status, int* rlist,
+                                                       int* rcount) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double qd[3];
+    load_point(pts, dtype, DIM, i, qd);
+    uint32_t st = 0;
+    float w = DIM == 2 ? query2_32(t, (float)qd[0], (float)qd[1], p.beta2, st)
+                       : query3_32(t, (float)qd[0], (float)qd[1], (float)qd[2], p.beta2, st, p.beta2_leaf);
+    double wd = (double)w;
+    if (near_half(wd, p.band) || (st & (GWN_QS_STACK_OVERFLOW | GWN_QS_UNRESOLVED))) rlist[atomicAdd(rcount, 1)] = (int)i;
+    out_w[i] = wd;
+    if (out_label) out_label[i] = (int)round(wd);
+    if (out_status) out_status[i] = st;
+}
+}  // namespace
+
+extern "C" gwn_status gwn_query_noalloc(gwn_model m, const void* points, int32_t dtype, size_t n, double* out_w,
+                                        int32_t* out_label, uint32_t* out_status, void* stream) {
+    if (!m) return fail(GWN_ERR_INVALID_ARG, "model is NULL");
+    if (m->device == GWN_DEVICE_HOST_ONLY) return fail(GWN_ERR_INVALID_ARG, "model was built host-only");
+    if (n == 0) return GWN_OK;
+    if (!points || !out_w) return fail(GWN_ERR_INVALID_ARG, "points and out_w are required");
+    if (dtype != GWN_F32 && dtype != GWN_F64) return fail(GWN_ERR_INVALID_ARG, "unknown points dtype");
+    if (n > kNoAllocMaxPoints)
+        return fail(GWN_ERR_INVALID_ARG, "gwn_query_noalloc takes at most " + std::to_string(kNoAllocMaxPoints) +
+                                             " points per call (its scratch array has a fixed size); split the batch");
+    DeviceGuard g(m->device);
+    int* scratch = nullptr;
+    gwn_status s = noalloc_scratch(m->device, &scratch);
+    if (s != GWN_OK) return s;
+    int* rcount = scratch;
+    int* rlist = scratch + kNoAllocHeader;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    QueryParams p{};
+    p.work = nullptr;
+    const double beta = m->opts.beta;
+    const double beta_leaf = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : beta;
+    p.beta2 = (float)(beta * beta);
+    p.beta2_leaf = (float)(beta_leaf * beta_leaf);
+    double br = m->opts.beta_repair;
+    if (br < 0) br = m->host.n_leaves <= 4096 ? 0.0 : 2.0 * beta;
+    p.beta2_repair = br > 0 ? br * br : 0.0;
+    p.band = (float)m->opts.repair_band;
+    p.mode = GWN_MODE_BVH;
+    p.precision = GWN_PREC_FP32_REPAIR;
+    // the array keeps the previous call's contents: the counter must start at zero
+    GWN_CUDA_TRY(cudaMemsetAsync(rcount, 0, sizeof(int), st));
+    const int B = 128;
+    const unsigned nb = (unsigned)((n + B - 1) / B);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned rb = (unsigned)std::min<long long>(std::max<long long>(nb, sms * 4), (long long)sms * 8);
+    if (m->dim == 2) {
+        k_query_noalloc<2><<<nb, B, 0, st>>>(m->tree, points, dtype, (long long)n, p, out_w, out_label, out_status, rlist, rcount);
+        k_repair<2><<<rb, B, 0, st>>>(m->tree, points, dtype, p, out_w, out_label, out_status, rlist, rcount);
+    } else {
+        k_query_noalloc<3><<<nb, B, 0, st>>>(m->tree, points, dtype, (long long)n, p, out_w, out_label, out_status, rlist, rcount);
+        k_repair<3><<<rb, B, 0, st>>>(m->tree, points, dtype, p, out_w, out_label, out_status, rlist, rcount);
+    }
+    GWN_CUDA_TRY(cudaGetLastError());
+    return GWN_OK;
+}
+
+extern "C" {
 
 gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
     if (!m || !out) return fail(GWN_ERR_INVALID_ARG, "NULL argument");

@@ -414,8 +414,8 @@ def main():
         serving = serving_leg(gwn, args.serve_seconds, log)
 
     # kernels per chunk of up to 2^19 points: bin, scan, scatter; 3 rounds of traversal, pair key, scan,
-    # pair scatter, pair eval, near band (+ round switch x2); overflow, finish, repair x3, counter accumulate
-    launches_per_step = sum(29 * math.ceil(p.shape[0] / (1 << 19)) for p in points)
+    # pair scatter, pair eval (+ round switch x2); near band, overflow, finish, repair x3, counter accumulate
+    launches_per_step = sum(27 * math.ceil(p.shape[0] / (1 << 19)) for p in points)
     line = {
         "metric": "GWN queries/s (batched containment, 16 trimmed-NURBS models)",
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),

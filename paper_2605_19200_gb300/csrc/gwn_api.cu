@@ -262,10 +262,11 @@ __global__ void __launch_bounds__(128) k_query32(DevTree t, const void* pts, int
 }
 
 template <int DIM>
-__device__ double query64(const DevTree& t, const double* q, double beta2, int mode, uint32_t& st) {
+__device__ double query64(const DevTree& t, const double* q, double beta2, int mode, uint32_t& st,
+                          double ratio = kRatio64Exact) {
     double b2 = (mode == GWN_MODE_DIRECT) ? 0.0 : beta2;
     if (DIM == 2) return query2_64(t, q[0], q[1], b2, st);
-    return query3_64(t, q[0], q[1], q[2], b2, st);
+    return query3_64(t, q[0], q[1], q[2], b2, st, ratio);
 }
 
 // FP64 pass over every query (precision GWN_PREC_FP64)
@@ -295,9 +296,9 @@ __global__ void k_iota(int n, int* list, int* count) {
 // lanes striding over the leaves, so that few repaired queries still fill the
 // FP64 pipes.
 template <int DIM>
-__device__ __forceinline__ double leaf64(const DevTree& t, int l, const double* q, uint32_t& st) {
+__device__ __forceinline__ double leaf64(const DevTree& t, int l, const double* q, uint32_t& st, double ratio) {
     if (DIM == 2) return leaf2_eval64(t, l, q[0], q[1], st);
-    return leaf3_eval64(t, l, q[0], q[1], q[2], st);
+    return leaf3_eval64(t, l, q[0], q[1], q[2], st, ratio);
 }
 
 template <int DIM>
@@ -306,13 +307,15 @@ __global__ void __launch_bounds__(128) k_repair(DevTree t, const void* pts, int 
                                                 const int* rcount) {
     int cnt = *rcount;
     bool direct = p.mode == GWN_MODE_DIRECT || !(p.beta2_repair > 0);
+    // the all-FP64 precision mode integrates to ~1e-8, the repair to ~1e-7
+    const double ratio = p.precision == GWN_PREC_FP64 ? kRatio64Exact : kRatio64Repair;
     if (!direct) {
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
             int i = rlist[k];
             double q[3];
             load_point(pts, dtype, DIM, i, q);
             uint32_t st = 0;
-            double w = query64<DIM>(t, q, p.beta2_repair, GWN_MODE_BVH, st);
+            double w = query64<DIM>(t, q, p.beta2_repair, GWN_MODE_BVH, st, ratio);
             out_w[i] = w;
             if (out_label) out_label[i] = (int)round(w);
             if (out_status) out_status[i] = (out_status[i] | st | GWN_QS_REPAIRED);
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(128) k_repair(DevTree t, const void* pts, int 
         load_point(pts, dtype, DIM, i, q);
         uint32_t st = 0;
         double w = 0.0;
-        for (int l = lane; l < t.n_leaves; l += 32) w += leaf64<DIM>(t, l, q, st);
+        for (int l = lane; l < t.n_leaves; l += 32) w += leaf64<DIM>(t, l, q, st, ratio);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             w += __shfl_xor_sync(0xffffffffu, w, off);
@@ -510,10 +513,13 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
                 k_pair_eval<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters, ws.pairs2,
                                                                ws.wacc, ws.st, ws.pairs64, ni, p.work);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[3], st));
-                k_pair_eval64<<<(unsigned)(sms * 2), B, 0, st>>>(m->tree, pts, dtype, ni, ws.counters, ws.pairs64, ws.wacc,
-                                                                 ws.st);
                 if (round < 2) k_next_round<<<1, 32, 0, st>>>(ws);
             }
+            // the near band of all rounds in one launch: a round only re-traverses
+            // points whose pairs overflowed, and those never enter the near band,
+            // so every listed point's FP32 sum is final here
+            k_pair_eval64_warp<<<(unsigned)(sms * 2), B, 0, st>>>(m->tree, pts, dtype, ni, ws.counters, ws.pairs64,
+                                                                  ws.wacc, ws.st);
             k_overflow3<<<(unsigned)(sms * 2), B, 0, st>>>(m->tree, pts, dtype, p.beta2, ws, ws.olist);
         }
         GWN_CUDA_TRY(cudaGetLastError());
@@ -525,19 +531,20 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         unsigned rb = (unsigned)std::min<long long>(std::max<long long>(nb, sms * 4), (long long)sms * 8);
         if (rb == 0) rb = 1;
         const unsigned wb = (unsigned)(sms * 4);  // blocks of kRepairWarps warps, one warp per repaired point
-        // 3D with beta_repair = 0 (exact sum over every leaf) still goes through the
-        // warp traversal: every leaf becomes an FP64 pair, and the pairs of all
-        // repaired points spread over the whole GPU instead of one warp per point
-        if (p.mode == GWN_MODE_DIRECT || (m->dim == 2 && !(p.beta2_repair > 0))) {
-            if (m->dim == 2) k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
-            else k_repair<3><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
+        // 3D always goes through the warp traversal and the FP64 pair list: with
+        // beta_repair = 0 or in direct mode (exact sum over every leaf) every leaf
+        // becomes a pair, and the pairs of all repaired points spread over the
+        // whole GPU instead of one warp walking all leaves per point
+        if (m->dim == 2 && (p.mode == GWN_MODE_DIRECT || !(p.beta2_repair > 0))) {
+            k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
         } else if (m->dim == 2) {
             k_rtrav_warp<2><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, p.beta2_repair, ws.rlist, ws, out_w,
                                                              out_label, out_status);
         } else {
-            k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, p.beta2_repair, ws.rlist, ws, out_w,
+            const double b2r = p.mode == GWN_MODE_DIRECT ? 0.0 : p.beta2_repair;
+            k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, b2r, ws.rlist, ws, out_w,
                                                              out_label, out_status);
-            k_rpairs3<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.rlist, ws);
+            k_rpairs3_warp<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.rlist, ws);
             k_rfinish<<<(unsigned)(sms * 2), B, 0, st>>>(ws.rlist, ws, out_w, out_label, out_status);
         }
         GWN_CUDA_TRY(cudaGetLastError());
@@ -950,7 +957,7 @@ gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
     for (int k = 0; k < 16; ++k) out[k] = 0;
     for (int k = 0; k < 4; ++k) out[k] = (int64_t)c[k];
     out[0] = (int64_t)(c[0] + c[7]);  // pairs over all rounds
-    out[2] = (int64_t)(c[2] + c[8]);  // near-band (FP64) pairs over all rounds
+    out[2] = (int64_t)c[2];           // near-band (FP64) pairs over all rounds
     out[3] = (int64_t)(c[6] + c[3]);  // points whose pairs overflowed in any round
     for (int k = 0; k < kWorkCount; ++k) out[4 + k] = (int64_t)wk[k];
     if (m->profiled) {

@@ -156,7 +156,7 @@ struct Workspace {
     int2* pairs2;     // pair capacity (sorted)
     int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
                       // [5] overflowed points of the current round (list input), [6] total overflow,
-                      // [7] pairs of finished rounds, [8] near-band pairs of finished rounds
+                      // [7] pairs of finished rounds
     int* olist;       // n: points whose pairs did not fit (rounds alternate with olist2)
     int* olist2;      // n
     unsigned long long* work;  // kWorkCount counters

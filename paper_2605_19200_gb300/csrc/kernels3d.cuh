@@ -37,11 +37,14 @@ constexpr int kLevel32 = 10;
 constexpr int kLevel64 = 30;
 // panel length / distance-to-q bound of the 8-point rule: the quadrature error
 // of an analytic integrand decays like rho^-16 with rho the Bernstein-ellipse
-// parameter, ~3.0 at 1.5 (FP32); FP64 uses 0.5, which measured ~1e-8 against
-// the oracle where 1.0 gave ~1e-7
-template <typename T> struct PanelRatio;
-template <> struct PanelRatio<float> { static constexpr float v = 1.5f; };
-template <> struct PanelRatio<double> { static constexpr double v = 0.5; };
+// parameter, ~3.0 at 1.5.  The FP32 bulk uses 1.5, and so does the FP64 near
+// band that completes it (there FP64 is needed for the geometry, not for the
+// quadrature).  The repair uses 1.0 (measured ~1e-7 against the oracle) and
+// the all-FP64 precision mode 0.5 (~1e-8).
+constexpr float kRatio32 = 1.5f;
+constexpr double kRatio64Band = 1.5;
+constexpr double kRatio64Repair = 1.0;
+constexpr double kRatio64Exact = 0.5;
 
 // binomial coefficients and the 8-point Gauss-Legendre rule on [0, 1]: device
 // constant memory, with host mirrors for host-side execution
@@ -128,6 +131,39 @@ GWN_HD inline void bern4(const G& g, int D, T t, T X[4], T dX[4]) {
     }
 }
 
+// the same for a degree known at compile time (the loops unroll and the point
+// loads become independent); FP32 takes the hardware reciprocal for r
+template <int D, typename T, typename G>
+GWN_HD inline void bern4_fixed(const G& g, T t, T X[4], T dX[4]) {
+    const bool rev = t > T(0.5);
+    const T a = rev ? T(1) - t : t;
+    const T b = T(1) - a;
+    const T r = a * Num<T>::inv_(b);
+    T acc[4], dacc[4], h[4];
+    g.pt(rev ? 0 : D, acc);
+#pragma unroll
+    for (int i = D - 1; i >= 0; --i) {
+        g.pt(rev ? D - i : i, h);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = acc[c] * r + h[c];
+    }
+    g.pt(D + 1 + (rev ? 0 : D - 1), dacc);
+#pragma unroll
+    for (int i = D - 2; i >= 0; --i) {
+        g.pt(D + 1 + (rev ? D - 1 - i : i), h);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dacc[c] = dacc[c] * r + h[c];
+    }
+    T pw = T(1);
+#pragma unroll
+    for (int e = 0; e < D - 1; ++e) pw *= b;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        X[c] = acc[c] * pw * b;
+        dX[c] = T(D) * dacc[c] * pw;
+    }
+}
+
 template <typename T> struct Gl8;
 template <> struct Gl8<float> {
     static GWN_HD inline float x(int k) { return GWN_GLXF(k); }
@@ -138,14 +174,54 @@ template <> struct Gl8<double> {
     static GWN_HD inline double w(int k) { return GWN_GLW(k); }
 };
 
-// int A_s(x(t) - q) . x'(t) dt over one boundary curve, adaptive; sets deep if
-// the panel limit was hit
+// the integrand A_s(x(t) - q) . x'(t) at parameter t of one boundary curve;
+// also the point x(t) and min(|r|^2, 2 |r| (|r| + s.r)): the integrand is
+// singular at q and along the string {q - t s}, and near the string
+// |r| (|r| + s.r) ~ (distance to the string)^2 / 2, so a panel must be short
+// relative to both distances
+template <int DF, typename T, typename G>
+GWN_HD inline T gl_node(const G& g, int D, T t, const T q[3], const T s[3], T x[3], T* dm2) {
+    T X[4], dX[4];
+    if (DF > 0) bern4_fixed<(DF > 0 ? DF : 1), T>(g, t, X, dX);
+    else bern4<T>(g, D, t, X, dX);
+    T iw = Num<T>::inv_(X[3]);
+    T x0 = X[0] * iw, x1 = X[1] * iw, x2 = X[2] * iw;
+    T d0 = (dX[0] - x0 * dX[3]) * iw, d1 = (dX[1] - x1 * dX[3]) * iw, d2 = (dX[2] - x2 * dX[3]) * iw;
+    T r0 = x0 - q[0], r1 = x1 - q[1], r2 = x2 - q[2];
+    T rr = r0 * r0 + r1 * r1 + r2 * r2;
+    T rn = sqrt(rr);
+    T sr = s[0] * r0 + s[1] * r1 + s[2] * r2;
+    T c0 = s[1] * r2 - s[2] * r1, c1 = s[2] * r0 - s[0] * r2, c2 = s[0] * r1 - s[1] * r0;
+    T den = rn * (rn + sr);
+    x[0] = x0; x[1] = x1; x[2] = x2;
+    *dm2 = fmin(rr, T(2) * den);
+    return (c0 * d0 + c1 * d1 + c2 * d2) * Num<T>::inv_(den);
+}
+
+// gl_node with the degree dispatched to the unrolled evaluators of the common
+// composed degrees (6 d for local pieces of degree d = 1, 2, 3; edges of the
+// leaf rectangle are degree-1 pieces)
 template <typename T, typename G>
-GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int maxlevel, bool& deep,
-                             WorkLocal* wl = nullptr) {
+GWN_HD inline T gl_node_any(const G& g, int D, T t, const T q[3], const T s[3], T x[3], T* dm2) {
+    switch (D) {
+        case 6: return gl_node<6, T>(g, D, t, q, s, x, dm2);
+        case 12: return gl_node<12, T>(g, D, t, q, s, x, dm2);
+        case 18: return gl_node<18, T>(g, D, t, q, s, x, dm2);
+        default: return gl_node<0, T>(g, D, t, q, s, x, dm2);
+    }
+}
+
+// int A_s(x(t) - q) . x'(t) dt over the panels of one boundary curve below panel
+// (level0, idx0) (panel idx of level L spans [idx, idx + 1] / 2^L), adaptive:
+// a panel is bisected until its length is at most `ratio` times its distance to
+// q and to the string; sets deep if the level limit was hit.
+template <int DF, typename T, typename G>
+GWN_HD T panel_subtree_d(const G& g, int D, const T q[3], const T s[3], int level0, unsigned idx0, int maxlevel, T ratio,
+                         bool& deep, WorkLocal* wl) {
+    const T ratio2 = ratio * ratio;
     T acc = 0;
-    int level = 0;
-    unsigned idx = 0;  // panel index at `level` (levels stay below 32)
+    int level = level0;
+    unsigned idx = idx0;  // panel index at `level` (levels stay below 32)
     while (true) {
         const T h = T(1) / T(1u << level);
         const T a = T(idx) * h;
@@ -153,28 +229,15 @@ GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int 
         T px = 0, py = 0, pz = 0;
 #pragma unroll 1
         for (int k = 0; k < 8; ++k) {
-            T X[4], dX[4];
-            bern4<T>(g, D, a + h * Gl8<T>::x(k), X, dX);
-            T iw = T(1) / X[3];
-            T x0 = X[0] * iw, x1 = X[1] * iw, x2 = X[2] * iw;
-            T d0 = (dX[0] - x0 * dX[3]) * iw, d1 = (dX[1] - x1 * dX[3]) * iw, d2 = (dX[2] - x2 * dX[3]) * iw;
-            T r0 = x0 - q[0], r1 = x1 - q[1], r2 = x2 - q[2];
-            T rr = r0 * r0 + r1 * r1 + r2 * r2;
-            T rn = sqrt(rr);
-            T sr = s[0] * r0 + s[1] * r1 + s[2] * r2;
-            T c0 = s[1] * r2 - s[2] * r1, c1 = s[2] * r0 - s[0] * r2, c2 = s[0] * r1 - s[1] * r0;
-            T den = rn * (rn + sr);
-            T f = (c0 * d0 + c1 * d1 + c2 * d2) / den;
+            T x[3], dm2;
+            T f = gl_node<DF, T>(g, D, a + h * Gl8<T>::x(k), q, s, x, &dm2);
             psum += Gl8<T>::w(k) * f;
-            // the integrand is singular at q and along the string {q - t s}; near
-            // the string |r| (|r| + s.r) ~ (distance to the string)^2 / 2, so the
-            // panel must be short relative to both distances
-            dmin2 = fmin(dmin2, fmin(rr, T(2) * den));
+            dmin2 = fmin(dmin2, dm2);
             if (k > 0) {
-                T e0 = x0 - px, e1 = x1 - py, e2 = x2 - pz;
+                T e0 = x[0] - px, e1 = x[1] - py, e2 = x[2] - pz;
                 len += sqrt(e0 * e0 + e1 * e1 + e2 * e2);
             }
-            px = x0; py = x1; pz = x2;
+            px = x[0]; py = x[1]; pz = x[2];
         }
         if (wl) {
             wl->v[kWorkGlNodes] += 8;
@@ -182,7 +245,7 @@ GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int 
         }
         // the 8 nodes span ~96% of the panel
         len *= T(1.1);
-        bool refine = len * len > T(PanelRatio<T>::v * PanelRatio<T>::v) * dmin2;
+        bool refine = len * len > ratio2 * dmin2;
         if (refine && level < maxlevel) {
             ++level;
             idx <<= 1;
@@ -190,14 +253,31 @@ GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int 
         }
         if (refine) deep = true;
         acc += psum * h;
-        while (idx & 1u) {
+        while (level > level0 && (idx & 1u)) {
             idx >>= 1;
             --level;
         }
-        if (level == 0) break;
+        if (level == level0) break;
         ++idx;
     }
     return acc;
+}
+
+template <typename T, typename G>
+GWN_HD T panel_subtree(const G& g, int D, const T q[3], const T s[3], int level0, unsigned idx0, int maxlevel, T ratio,
+                       bool& deep, WorkLocal* wl = nullptr) {
+    switch (D) {
+        case 6: return panel_subtree_d<6, T>(g, D, q, s, level0, idx0, maxlevel, ratio, deep, wl);
+        case 12: return panel_subtree_d<12, T>(g, D, q, s, level0, idx0, maxlevel, ratio, deep, wl);
+        case 18: return panel_subtree_d<18, T>(g, D, q, s, level0, idx0, maxlevel, ratio, deep, wl);
+        default: return panel_subtree_d<0, T>(g, D, q, s, level0, idx0, maxlevel, ratio, deep, wl);
+    }
+}
+
+template <typename T, typename G>
+GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int maxlevel, T ratio, bool& deep,
+                             WorkLocal* wl = nullptr) {
+    return panel_subtree<T>(g, D, q, s, 0, 0u, maxlevel, ratio, deep, wl);
 }
 
 // S, S_u, S_v of the leaf's bicubic net at local (u, v)
@@ -379,7 +459,7 @@ GWN_HD int leaf_hit(const DevTree& t, const Leaf3Info& I, const G& g, const T q[
 // GWN of leaf li at q (q relative to the leaf geometry's origin); false if the
 // precision of T could not resolve it
 template <typename T, typename G>
-GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T q[3], T* out, int maxlevel,
+GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T q[3], T* out, int maxlevel, T ratio,
                        WorkLocal* wl = nullptr) {
     if (wl) wl->v[kWorkLeaves] += 1;
     T nrm[3] = {(T)I.nrm[0], (T)I.nrm[1], (T)I.nrm[2]};
@@ -411,19 +491,20 @@ GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T
         G gc = g;
         if (sizeof(T) == 4) gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts + ci.ctrl_off);
         else gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts64 + (size_t)ci.ctrl_off * 4);
-        acc += (T)ci.mult * curve_line_integral<T>(gc, ci.deg, q, s, maxlevel, deep, wl);
+        acc += (T)ci.mult * curve_line_integral<T>(gc, ci.deg, q, s, maxlevel, ratio, deep, wl);
     }
     if (deep) return false;
     *out = acc * T(0.07957747154594767) - hits;  // 1 / (4 pi)
     return true;
 }
 
-GWN_HD inline double leaf3_eval64(const DevTree& t, int li, double qx, double qy, double qz, uint32_t& st) {
+GWN_HD inline double leaf3_eval64(const DevTree& t, int li, double qx, double qy, double qz, uint32_t& st,
+                                  double ratio = kRatio64Exact) {
     Leaf3Info I = t.leaf3[li];
     Geo64 g{t.net3_64 + (size_t)li * 64, nullptr};
     double q[3] = {qx, qy, qz};
     double w = 0;
-    if (!leaf3_core<double>(t, I, g, q, &w, kLevel64)) st |= GWN_QS_UNRESOLVED;
+    if (!leaf3_core<double>(t, I, g, q, &w, kLevel64, ratio)) st |= GWN_QS_UNRESOLVED;
     return w;
 }
 
@@ -434,15 +515,134 @@ GWN_HD inline bool leaf3_try32(const DevTree& t, int li, float qx, float qy, flo
     Geo32 g{t.net3 + (size_t)li * kNet3Vec, nullptr};
     float q[3] = {qx - I.cen[0], qy - I.cen[1], qz - I.cen[2]};
     *w = 0.f;
-    return leaf3_core<float>(t, I, g, q, w, kLevel32, wl);
+    return leaf3_core<float>(t, I, g, q, w, kLevel32, kRatio32, wl);
 }
 
 GWN_HD inline float leaf3_eval32(const DevTree& t, int li, float qx, float qy, float qz, uint32_t& st) {
     float w;
     if (leaf3_try32(t, li, qx, qy, qz, &w)) return w;
     st |= GWN_QS_NEAR;
-    return (float)leaf3_eval64(t, li, (double)qx, (double)qy, (double)qz, st);
+    return (float)leaf3_eval64(t, li, (double)qx, (double)qy, (double)qz, st, kRatio64Band);
 }
+
+// ---- One FP64 leaf evaluation spread over a warp (near band and repair).
+// In one thread, an evaluation close to a boundary curve runs hundreds of
+// Gauss-Legendre nodes one after another at FP64 latency, and such a single
+// pair bounds the duration of its whole launch.  Here lane 0 does the crossing
+// test, then the warp works through the adaptive panels of all boundary curves
+// as a shared list (in shared memory, `stk`, kQuadStack entries): four panels
+// per step, one Gauss-Legendre node per lane, the 8 lanes of a panel reducing
+// its sum, distance and length with shuffles.  A panel that fails the length
+// test pushes its two halves; when the list is full its group's leader
+// integrates the panel's subtree alone.  Same arithmetic as leaf3_core<double>
+// up to the order of the additions.  Returns false (w undefined) where
+// leaf3_core would.
+constexpr int kQuadStack = 256;
+
+#if defined(__CUDACC__)
+__device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3], double ratio, int maxlevel, int2* stk,
+                                    double* out) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, grp = lane >> 3, k = lane & 7;
+    const Leaf3Info I = t.leaf3[li];
+    const Geo64 g{t.net3_64 + (size_t)li * 64, nullptr};
+    const double nrm[3] = {(double)I.nrm[0], (double)I.nrm[1], (double)I.nrm[2]};
+    const double dq[3] = {q[0] - (double)I.cen[0], q[1] - (double)I.cen[1], q[2] - (double)I.cen[2]};
+    const double d2 = dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2];
+    const double rfar = 1.1 * (double)I.rad;
+    double s[3];
+    double hits = 0;
+    if (d2 > rfar * rfar) {
+        double l = Num<double>::rsqrt_(d2);
+        s[0] = -dq[0] * l; s[1] = -dq[1] * l; s[2] = -dq[2] * l;
+    } else {
+        double sig = (dq[0] * nrm[0] + dq[1] * nrm[1] + dq[2] * nrm[2]) >= 0 ? 1.0 : -1.0;
+        s[0] = -sig * nrm[0]; s[1] = -sig * nrm[1]; s[2] = -sig * nrm[2];
+        int hr = kHitNone;
+        if (lane == 0) hr = leaf_hit<double>(t, I, g, q, nrm, sig, (double)I.diag, &hits, kMaxLevel64);
+        hr = __shfl_sync(full, hr, 0);
+        hits = __shfl_sync(full, hits, 0);
+        if (hr == kHitUnsure) return false;
+    }
+    const double ratio2 = ratio * ratio;
+    double acc = 0;
+    bool deep = false;
+    int sp = 0, next_curve = 0;
+    __syncwarp();
+    while (true) {
+        // curves not started yet enter the list while it has room
+        const int add = min(kQuadStack - sp, I.c3_cnt - next_curve);
+        for (int j = lane; j < add; j += 32) stk[sp + j] = make_int2(next_curve + j, 0);
+        sp += add;
+        next_curve += add;
+        __syncwarp();
+        if (sp == 0) break;
+        const int take = min(sp, 4);
+        int2 task = make_int2(-1, 0);
+        if (grp < take) task = stk[sp - 1 - grp];
+        sp -= take;
+        __syncwarp();
+        const bool act = task.x >= 0;
+        int level = 0, cidx = 0;
+        unsigned idx = 0;
+        double h = 1, f = 0, dm2 = 1e300, x[3] = {0, 0, 0};
+        Curve3Info ci{};
+        Geo64 gc = g;
+        if (act) {
+            cidx = task.x & 0xffff;
+            level = task.x >> 16;
+            idx = (unsigned)task.y;
+            ci = t.c3[I.c3_off + cidx];
+            gc.pts = t.c3pts64 + (size_t)ci.ctrl_off * 4;
+            h = 1.0 / double(1u << level);
+            f = gl_node_any<double>(gc, ci.deg, double(idx) * h + h * Gl8<double>::x(k), q, s, x, &dm2);
+        }
+        const double p0 = __shfl_up_sync(full, x[0], 1), p1 = __shfl_up_sync(full, x[1], 1),
+                     p2 = __shfl_up_sync(full, x[2], 1);
+        double seg = 0;
+        if (act && k > 0) {
+            const double e0 = x[0] - p0, e1 = x[1] - p1, e2 = x[2] - p2;
+            seg = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+        }
+        double psum = act ? Gl8<double>::w(k) * f : 0.0;
+        for (int off = 1; off < 8; off <<= 1) {
+            psum += __shfl_xor_sync(full, psum, off);
+            seg += __shfl_xor_sync(full, seg, off);
+            dm2 = fmin(dm2, __shfl_xor_sync(full, dm2, off));
+        }
+        const double len = seg * 1.1;  // the 8 nodes span ~96% of the panel
+        const bool refine = act && len * len > ratio2 * dm2;
+        const bool split = refine && level < maxlevel;
+        if (refine && !split) deep = true;
+        if (act && !split && k == 0) acc += (double)ci.mult * psum * h;
+        // the halves of split panels go to the list (positions by a prefix sum over the leaders)
+        const int npush = (split && k == 0) ? 2 : 0;
+        int incl = npush;
+        for (int off = 1; off < 32; off <<= 1) {
+            int v = __shfl_up_sync(full, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int total = __shfl_sync(full, incl, 31);
+        if (sp + total <= kQuadStack) {
+            if (npush) {
+                const int cl = cidx | ((level + 1) << 16);
+                stk[sp + incl - 2] = make_int2(cl, (int)(2u * idx + 1u));
+                stk[sp + incl - 1] = make_int2(cl, (int)(2u * idx));
+            }
+            sp += total;
+        } else if (npush) {
+            bool dp = false;
+            acc += (double)ci.mult * panel_subtree<double>(gc, ci.deg, q, s, level, idx, maxlevel, ratio, dp);
+            if (dp) deep = true;
+        }
+        __syncwarp();
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(full, acc, off);
+    if (__any_sync(full, deep)) return false;
+    *out = acc * 0.07957747154594767 - hits;  // 1 / (4 pi)
+    return true;
+}
+#endif
 
 template <typename T>
 GWN_HD inline T far3_eval(const T* f, T rx, T ry, T rz) {
@@ -504,10 +704,11 @@ GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float bet
 }
 
 // Algorithm 1 in FP64 (repair pass); beta2 <= 0 evaluates every leaf directly
-GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, double beta2, uint32_t& st) {
+GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, double beta2, uint32_t& st,
+                        double ratio = kRatio64Exact) {
     double w = 0.0;
     if (beta2 <= 0.0) {
-        for (int i = 0; i < t.n_leaves; ++i) w += leaf3_eval64(t, i, qx, qy, qz, st);
+        for (int i = 0; i < t.n_leaves; ++i) w += leaf3_eval64(t, i, qx, qy, qz, st, ratio);
         return w;
     }
     int stack[kStack64];
@@ -525,7 +726,7 @@ GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, doubl
                     done = true;
                 }
             }
-            if (!done) w += leaf3_eval64(t, li, qx, qy, qz, st);
+            if (!done) w += leaf3_eval64(t, li, qx, qy, qz, st, ratio);
         } else {
             const double* h = t.hdr64 + (size_t)node * 4;
             double rx = h[0] - qx, ry = h[1] - qy, rz = h[2] - qz;

@@ -240,7 +240,7 @@ __global__ void k_pair_scatter(long long npair_cap, const int* counters, const i
     }
 }
 
-__global__ void __launch_bounds__(128) k_pair_eval(DevTree t, const void* pts, int dtype, long long npair_cap,
+__global__ void __launch_bounds__(128, 5) k_pair_eval(DevTree t, const void* pts, int dtype, long long npair_cap,
                                                    int* counters, const int2* pairs, float* wacc, uint32_t* st,
                                                    int2* pairs64, int npair64_cap, unsigned long long* work) {
     WorkLocal wl = {};
@@ -277,9 +277,36 @@ __global__ void k_pair_eval64(DevTree t, const void* pts, int dtype, int npair64
             q[0] = (double)(float)p[0]; q[1] = (double)(float)p[1]; q[2] = (double)(float)p[2];
         }
         uint32_t s = 0;
-        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s);
+        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s, kRatio64Band);
         atomicAdd(&wacc[pr.x], (float)v);
         if (s) atomicOr(&st[pr.x], s);
+    }
+}
+
+// the near band with one warp per pair (leaf3_warp64)
+__global__ void __launch_bounds__(128) k_pair_eval64_warp(DevTree t, const void* pts, int dtype, int npair64_cap,
+                                                          const int* counters, const int2* pairs64, float* wacc,
+                                                          uint32_t* st) {
+    __shared__ int2 sstk[4][kQuadStack];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int np = min(counters[2], npair64_cap);
+    for (int k = blockIdx.x * 4 + wid; k < np; k += gridDim.x * 4) {
+        const int2 pr = pairs64[k];
+        double q[3];
+        if (dtype == GWN_F32) {
+            const float* p = reinterpret_cast<const float*>(pts) + (size_t)pr.x * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        } else {
+            const double* p = reinterpret_cast<const double*>(pts) + (size_t)pr.x * 3;
+            q[0] = (double)(float)p[0]; q[1] = (double)(float)p[1]; q[2] = (double)(float)p[2];
+        }
+        double v = 0;
+        const bool ok = leaf3_warp64(t, pr.y, q, kRatio64Band, kLevel64, sstk[wid], &v);
+        if (lane == 0) {
+            atomicAdd(&wacc[pr.x], ok ? (float)v : 0.f);
+            if (!ok) atomicOr(&st[pr.x], GWN_QS_UNRESOLVED);
+        }
+        __syncwarp();
     }
 }
 
@@ -354,7 +381,7 @@ __global__ void __launch_bounds__(128) k_rtrav3(DevTree t, const void* pts, int 
                 } else {
                     long long slot = atomicAdd(&ws.counters[4], 1);
                     if (slot < kRepairPairCap) ws.rpairs[slot] = make_int2(k, li);
-                    else w += leaf3_eval64(t, li, q[0], q[1], q[2], st);
+                    else w += leaf3_eval64(t, li, q[0], q[1], q[2], st, kRatio64Repair);
                 }
             } else {
                 const double* h = t.hdr64 + (size_t)node * 4;
@@ -390,9 +417,36 @@ __global__ void __launch_bounds__(128) k_rpairs3(DevTree t, const void* pts, int
             q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
         }
         uint32_t s = 0;
-        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s);
+        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s, kRatio64Repair);
         atomicAdd(&ws.rw[pr.x], v);
         if (s) atomicOr(&ws.st[qi], s);
+    }
+}
+
+// FP64 repair pairs with one warp per pair (leaf3_warp64)
+__global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts, int dtype, const int* rlist,
+                                                      Workspace ws) {
+    __shared__ int2 sstk[4][kQuadStack];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long np = min((long long)ws.counters[4], kRepairPairCap);
+    for (long long j = (long long)blockIdx.x * 4 + wid; j < np; j += (long long)gridDim.x * 4) {
+        const int2 pr = ws.rpairs[j];
+        const int qi = rlist[pr.x];
+        double q[3];
+        if (dtype == GWN_F32) {
+            const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        } else {
+            const double* p = reinterpret_cast<const double*>(pts) + (size_t)qi * 3;
+            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+        }
+        double v = 0;
+        const bool ok = leaf3_warp64(t, pr.y, q, kRatio64Repair, kLevel64, sstk[wid], &v);
+        if (lane == 0) {
+            if (ok) atomicAdd(&ws.rw[pr.x], v);
+            else atomicOr(&ws.st[qi], GWN_QS_UNRESOLVED);
+        }
+        __syncwarp();
     }
 }
 
@@ -403,10 +457,8 @@ __global__ void k_next_round(Workspace ws) {
         ws.counters[5] = ws.counters[3];
         ws.counters[6] += ws.counters[3];
         ws.counters[7] += ws.counters[0];  // pairs of the finished round
-        ws.counters[8] += ws.counters[2];  // near-band pairs of the finished round
         ws.counters[3] = 0;
-        ws.counters[0] = 0;
-        ws.counters[2] = 0;
+        ws.counters[0] = 0;  // the near-band list (counters[2]) spans all rounds
     }
 }
 
@@ -483,7 +535,7 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
                         } else {
                             int slot = atomicAdd(&ws.counters[4], 1);
                             if (slot < kRepairPairCap) ws.rpairs[slot] = make_int2(k, li);
-                            else acc += leaf3_eval64(t, li, q[0], q[1], q[2], st);
+                            else acc += leaf3_eval64(t, li, q[0], q[1], q[2], st, kRatio64Repair);
                         }
                     }
                 } else {

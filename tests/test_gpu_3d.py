@@ -142,3 +142,24 @@ def test_autotuned_beta_meets_tolerance(oracle_lib):
     w = w.cpu().numpy()[sel]
     ok = np.isfinite(w_ref)
     assert np.max(np.abs(w[ok] - w_ref[ok])) <= 1e-4
+
+
+@pytest.mark.parametrize("beta_repair,tol", [(0.0, 1e-6), (12.0, 1e-4)])
+def test_repair_of_most_points(oracle_lib, beta_repair, tol):
+    """The trimmed sphere is an open surface, so its GWN takes every value in
+    (0, 1); a repair band of 0.4999 then sends almost every query through the
+    FP64 repair (warp traversal and the FP64 pair list, one warp per pair).
+    With beta_repair = 0 the repair is the exact sum over every leaf, held to
+    1e-6; with beta_repair = 12 its far field is Taylor, held to 1e-4."""
+    patches, q = configs.sphere_3d(n_queries=3000)
+    sel = q[:500]
+    w_ref, fl = oracle_lib.gwn3d(patches, sel, near_thr=1e-6 * _diag(patches))
+    ok = np.isfinite(w_ref)
+    m = gwn.gwn_build_3d(patches, beta=6.0, beta_leaf=4.0, repair_band=0.4999, beta_repair=beta_repair)
+    w, lab, st = m.query(_q(sel.astype(np.float32)))
+    w, st = w.cpu().numpy(), st.cpu().numpy()
+    rep = ok & ((st & gwn.QS_REPAIRED) != 0)
+    assert rep.sum() > 0.5 * ok.sum()
+    assert not np.any(st[ok] & gwn.QS_UNRESOLVED)
+    assert np.max(np.abs(w[rep] - w_ref[rep])) <= tol
+    assert np.max(np.abs(w[ok] - w_ref[ok])) <= 1e-4

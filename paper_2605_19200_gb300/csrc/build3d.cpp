@@ -823,7 +823,8 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
             ci.mult = (float)L.mult[b];
             ci.pad = 0.f;
             out->c3.push_back(ci);
-            // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i);
+            // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i),
+            // then the same 2 D + 1 points of the reversed curve (evaluation for t > 1/2);
             // float copies relative to the leaf centre, double copies absolute
             std::vector<double> rel((size_t)(D + 1) * 4);
             for (int t = 0; t <= D; ++t) {
@@ -842,6 +843,19 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
                     out->c3pts64.push_back(c * (X[(size_t)(t + 1) * 4 + k] - X[(size_t)t * 4 + k]));
                 }
                 out->c3pts.push_back(float4{f[0], f[1], f[2], f[3]});
+            }
+            {
+                // reversed copy: R_i = P_{D-i}, RQ_i = Q_{D-1-i}
+                const size_t f0 = (size_t)ci.ctrl_off, d0 = (size_t)ci.ctrl_off * 4;
+                for (int t = 0; t <= D; ++t) {
+                    out->c3pts.push_back(out->c3pts[f0 + (size_t)(D - t)]);
+                    for (int k = 0; k < 4; ++k) out->c3pts64.push_back(out->c3pts64[d0 + (size_t)(D - t) * 4 + k]);
+                }
+                for (int t = 0; t < D; ++t) {
+                    out->c3pts.push_back(out->c3pts[f0 + (size_t)(D + 1 + D - 1 - t)]);
+                    for (int k = 0; k < 4; ++k)
+                        out->c3pts64.push_back(out->c3pts64[d0 + (size_t)(D + 1 + D - 1 - t) * 4 + k]);
+                }
             }
             TP e3 = tp_elevate3(L.bnd[b]);
             float f[12];

@@ -65,8 +65,9 @@ struct Leaf3Info {
 // A 3D boundary curve: rational Bezier of degree D = deg (<= kMaxC3Deg) stored
 // from ctrl_off in the curve-point array as D + 1 homogeneous points scaled by
 // their binomial coefficients C(D, i) c_i, followed by the D derivative points
-// C(D-1, i) (c_{i+1} - c_i), and counted `mult` times (winding multiplicity of a
-// clipped rectangle edge).
+// C(D-1, i) (c_{i+1} - c_i), then the same 2 D + 1 points of the reversed
+// curve (evaluation for t > 1/2 reads them in forward order), and counted `mult`
+// times (winding multiplicity of a clipped rectangle edge).
 constexpr int kMaxC3Deg = 18;
 struct Curve3Info {
     int32_t ctrl_off;

@@ -31,15 +31,23 @@ template <> struct Num<float> {
 #if defined(__CUDA_ARCH__)
     static GWN_HD inline float inv_(float x) { return __frcp_rn(x); }
     static GWN_HD inline float rsqrt_(float x) { return rsqrtf(x); }
+    // approximate reciprocal and square root (a few ulp) for the FP32 bulk of the
+    // quadrature, whose error budget is 1e-4; sqrt_fast(0) is NaN
+    static GWN_HD inline float rcp_fast(float x) { return __fdividef(1.0f, x); }
+    static GWN_HD inline float sqrt_fast(float x) { return x * rsqrtf(x); }
 #else
     static GWN_HD inline float inv_(float x) { return 1.0f / x; }
     static GWN_HD inline float rsqrt_(float x) { return 1.0f / sqrtf(x); }
+    static GWN_HD inline float rcp_fast(float x) { return 1.0f / x; }
+    static GWN_HD inline float sqrt_fast(float x) { return sqrtf(x); }
 #endif
     static constexpr float inv2pi = 0.15915494309189535f;
 };
 template <> struct Num<double> {
     static GWN_HD inline double atan2_(double y, double x) { return atan2(y, x); }
     static GWN_HD inline double inv_(double x) { return 1.0 / x; }
+    static GWN_HD inline double rcp_fast(double x) { return 1.0 / x; }
+    static GWN_HD inline double sqrt_fast(double x) { return sqrt(x); }
 #if defined(__CUDA_ARCH__)
     static GWN_HD inline double rsqrt_(double x) { return rsqrt(x); }
 #else

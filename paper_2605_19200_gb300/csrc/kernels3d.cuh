@@ -72,6 +72,7 @@ static float h_glx8f[8], h_glw8f[8];
 
 // accessors of one leaf's geometry, in FP32 (relative to the leaf centre) or FP64 (absolute)
 struct Geo32 {
+    static constexpr int kPtStride = 1;  // array elements per curve point
     const float4* net;
     const float4* pts;
     GWN_HD inline void net_pt(int k, float h[4]) const {
@@ -84,6 +85,7 @@ struct Geo32 {
     }
 };
 struct Geo64 {
+    static constexpr int kPtStride = 4;
     const double* net;
     const double* pts;
     GWN_HD inline void net_pt(int k, double h[4]) const {
@@ -101,20 +103,22 @@ struct Geo64 {
 //   X(t)  = (1 - a)^D     sum_i P_i r^i
 //   X'(t) = D (1 - a)^(D-1) sum_i Q_i r^i
 template <typename T, typename G>
-GWN_HD inline void bern4(const G& g, int D, T t, T X[4], T dX[4]) {
+GWN_HD inline void bern4(const G& g0, int D, T t, T X[4], T dX[4]) {
     const bool rev = t > T(0.5);
     const T a = rev ? T(1) - t : t;
     const T b = T(1) - a;
-    const T r = a / b;
+    const T r = a * Num<T>::rcp_fast(b);
+    G g = g0;
+    if (rev) g.pts += (size_t)(2 * D + 1) * G::kPtStride;  // the reversed copy
     T acc[4], dacc[4], h[4];
-    g.pt(rev ? 0 : D, acc);
+    g.pt(D, acc);
     for (int i = D - 1; i >= 0; --i) {
-        g.pt(rev ? D - i : i, h);
+        g.pt(i, h);
         for (int c = 0; c < 4; ++c) acc[c] = acc[c] * r + h[c];
     }
-    g.pt(D + 1 + (rev ? 0 : D - 1), dacc);
+    g.pt(D + 1 + D - 1, dacc);
     for (int i = D - 2; i >= 0; --i) {
-        g.pt(D + 1 + (rev ? D - 1 - i : i), h);
+        g.pt(D + 1 + i, h);
         for (int c = 0; c < 4; ++c) dacc[c] = dacc[c] * r + h[c];
     }
     // b^(D-1) by repeated squaring
@@ -134,23 +138,25 @@ GWN_HD inline void bern4(const G& g, int D, T t, T X[4], T dX[4]) {
 // the same for a degree known at compile time (the loops unroll and the point
 // loads become independent); FP32 takes the hardware reciprocal for r
 template <int D, typename T, typename G>
-GWN_HD inline void bern4_fixed(const G& g, T t, T X[4], T dX[4]) {
+GWN_HD inline void bern4_fixed(const G& g0, T t, T X[4], T dX[4]) {
     const bool rev = t > T(0.5);
     const T a = rev ? T(1) - t : t;
     const T b = T(1) - a;
-    const T r = a * Num<T>::inv_(b);
+    const T r = a * Num<T>::rcp_fast(b);
+    G g = g0;
+    if (rev) g.pts += (size_t)(2 * D + 1) * G::kPtStride;  // the reversed copy
     T acc[4], dacc[4], h[4];
-    g.pt(rev ? 0 : D, acc);
+    g.pt(D, acc);
 #pragma unroll
     for (int i = D - 1; i >= 0; --i) {
-        g.pt(rev ? D - i : i, h);
+        g.pt(i, h);
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] = acc[c] * r + h[c];
     }
-    g.pt(D + 1 + (rev ? 0 : D - 1), dacc);
+    g.pt(D + 1 + D - 1, dacc);
 #pragma unroll
     for (int i = D - 2; i >= 0; --i) {
-        g.pt(D + 1 + (rev ? D - 1 - i : i), h);
+        g.pt(D + 1 + i, h);
 #pragma unroll
         for (int c = 0; c < 4; ++c) dacc[c] = dacc[c] * r + h[c];
     }
@@ -184,18 +190,18 @@ GWN_HD inline T gl_node(const G& g, int D, T t, const T q[3], const T s[3], T x[
     T X[4], dX[4];
     if (DF > 0) bern4_fixed<(DF > 0 ? DF : 1), T>(g, t, X, dX);
     else bern4<T>(g, D, t, X, dX);
-    T iw = Num<T>::inv_(X[3]);
+    T iw = Num<T>::rcp_fast(X[3]);
     T x0 = X[0] * iw, x1 = X[1] * iw, x2 = X[2] * iw;
     T d0 = (dX[0] - x0 * dX[3]) * iw, d1 = (dX[1] - x1 * dX[3]) * iw, d2 = (dX[2] - x2 * dX[3]) * iw;
     T r0 = x0 - q[0], r1 = x1 - q[1], r2 = x2 - q[2];
     T rr = r0 * r0 + r1 * r1 + r2 * r2;
-    T rn = sqrt(rr);
+    T rn = Num<T>::sqrt_fast(rr);
     T sr = s[0] * r0 + s[1] * r1 + s[2] * r2;
     T c0 = s[1] * r2 - s[2] * r1, c1 = s[2] * r0 - s[0] * r2, c2 = s[0] * r1 - s[1] * r0;
     T den = rn * (rn + sr);
     x[0] = x0; x[1] = x1; x[2] = x2;
     *dm2 = fmin(rr, T(2) * den);
-    return (c0 * d0 + c1 * d1 + c2 * d2) * Num<T>::inv_(den);
+    return (c0 * d0 + c1 * d1 + c2 * d2) * Num<T>::rcp_fast(den);
 }
 
 // gl_node with the degree dispatched to the unrolled evaluators of the common
@@ -235,7 +241,7 @@ GWN_HD T panel_subtree_d(const G& g, int D, const T q[3], const T s[3], int leve
             dmin2 = fmin(dmin2, dm2);
             if (k > 0) {
                 T e0 = x[0] - px, e1 = x[1] - py, e2 = x[2] - pz;
-                len += sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+                len += Num<T>::sqrt_fast(e0 * e0 + e1 * e1 + e2 * e2);
             }
             px = x[0]; py = x[1]; pz = x[2];
         }

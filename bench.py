@@ -40,6 +40,7 @@ import numpy as np
 BETA = 0.0              # 0: the build's autotuner picks beta and beta_leaf per model for max |dGWN| <= 1e-4
 DIRECT_SAMPLE = 40960   # queries per model for the plain direct-sum comparison (fills the GPU)
 ORACLE_SAMPLE = 2       # queries per model for the CPU oracle
+PAIR_EVAL_DRAM_BYTES_PER_PAIR = 10.5  # ncu dram__bytes_read + dram__bytes_write of k_pair_eval per pair
 
 
 def build_workload(scale_queries: float = 1.0, n_models: int = 16):
@@ -254,6 +255,8 @@ def main():
     ap.add_argument("--beta", type=float, default=BETA)
     ap.add_argument("--beta-leaf", type=float, default=0.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="streams of the batched query (one graph launch per step); 0 = one gwn_query per model")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving phase")
     ap.add_argument("--kernels-only", action="store_true",
                     help="timed steps only (no e2e, direct-sum or CPU legs); for profiler runs")
@@ -294,10 +297,15 @@ def main():
     n_leaves = sum(m.info()["n_leaves"] for m in models)
     n_patches = sum(len(p) for p, _ in workload)
     stream = torch.cuda.current_stream(dev)
+    batch = gwn.Batch(n_streams=args.streams) if args.streams > 0 else None
 
     def step():
-        for m, p, o in zip(models, points, outs):
-            m.query(p, out=o, stream=stream)
+        if batch is not None:
+            # all models and point sets in one CUDA-graph launch (captured on the first call)
+            batch.query(models, points, outs, stream=stream)
+        else:
+            for m, p, o in zip(models, points, outs):
+                m.query(p, out=o, stream=stream)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -356,19 +364,36 @@ def main():
     d_us, d_fl = (leaf_us, fl_leaf) if dominant == "k_pair_eval" else (trav_us, fl_trav)
     # per launch: algorithmic flops / event-timed duration (summed over the 16 launches of a step)
     achieved = d_fl / (d_us * 1e-6) / 1e12
+    # DRAM bytes (read + written) per (query, leaf) pair of k_pair_eval, from one ncu capture of
+    # this kernel on a one-model case, scaled to the average launch of a step by its pairs
+    n_pair_launches = sum(3 * math.ceil(p.shape[0] / (1 << 19)) for p in points)
+    traffic = (PAIR_EVAL_DRAM_BYTES_PER_PAIR * pairs / n_pair_launches
+               if dominant == "k_pair_eval" and pairs > 0 else None)
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": "DRAM bytes per average k_pair_eval launch: 10.5 B per pair (ncu, one-model "
+                                "capture) x pairs of a step / launches of a step",
                 "peak_note": f"FP32 FMA issue: {sms} SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median under load)",
                 "trav_ms_per_step": trav_us / 1e3, "leaf_ms_per_step": leaf_us / 1e3}
 
-    # e2e through the C ABI with pinned host buffers (copies in the timed region)
+    # e2e through the public API with pinned host buffers: every step copies the
+    # points in, runs the query and copies values and labels back (in the timed region)
     host_pts = [p.cpu().pin_memory() for p in points]
     host_out = [(torch.empty(p.shape[0], dtype=torch.float64).pin_memory(),
                  torch.empty(p.shape[0], dtype=torch.int32).pin_memory(), None) for p in points]
+    dev_pts = [torch.empty_like(p) for p in points]
 
     def step_e2e():
-        for m, hp, ho in zip(models, host_pts, host_out):
-            gwn.gwn_query(m, hp, out=ho, want_status=False, stream=stream)
+        if batch is not None:
+            for hp, dp in zip(host_pts, dev_pts):
+                dp.copy_(hp, non_blocking=True)
+            batch.query(models, dev_pts, outs, stream=stream)
+            for o, ho in zip(outs, host_out):
+                ho[0].copy_(o[0], non_blocking=True)
+                ho[1].copy_(o[1], non_blocking=True)
+        else:
+            for m, hp, ho in zip(models, host_pts, host_out):
+                gwn.gwn_query(m, hp, out=ho, want_status=False, stream=stream)
 
     step_e2e()
     torch.cuda.synchronize()
@@ -427,7 +452,9 @@ def main():
                    "beta": "autotuned" if args.beta == 0 else args.beta, "beta_per_model": tuned,
                    "tolerance": 1e-4, "order": 2, "precision": "fp32 bulk + fp64 repair",
                    "l2": f"inputs larger than L2 ({total_q * 12 / 1e6:.0f} MB of points per step)",
-                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1)},
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1),
+                   "launch": (f"gwn_query_batch: one CUDA graph launch per step over {args.streams} streams"
+                              if batch is not None else "one gwn_query per model")},
         "e2e": {"value": world * total_q / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roofline,

@@ -104,7 +104,7 @@ typedef struct {
     double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2, or 0 = choose
                              beta (and beta_leaf) by the autotuner to meet `tolerance` (default 2) */
     double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves;
-                             < 0 = automatic: direct sum up to 4096 leaves, else 2 x beta (default -1) */
+                             < 0 = automatic: direct sum up to 512 leaves, else 3 x beta (default -1) */
     double repair_band;   /* re-evaluate in FP64 when |w - round(w) +- 1/2| < band (default 1e-3) */
     int32_t quad_nodes;   /* Gauss-Legendre nodes per rule for 3D moments (default 10) */
     int32_t precision;    /* GWN_PREC_* (default GWN_PREC_FP32_REPAIR) */
@@ -230,6 +230,45 @@ gwn_status gwn_model_leaves(gwn_model model, int64_t* prim, double* param);
  * m1_ij = int (x - x0)_i n_j and m2_ijk = int (x - x0)_i (x - x0)_j n_k.
  * Any pointer may be NULL. */
 gwn_status gwn_model_tree(gwn_model model, int32_t* child, double* x0, double* r, double* mom);
+
+/* ---------------------------------------------------------------- batches
+ * Many models and point sets in one launch.  Algorithm 1 is stated for one
+ * model; a batch runs the query of each item (its own model, points and
+ * outputs, all device memory) through the same pipeline as gwn_query with the
+ * model's build options, the items spread over a pool of CUDA streams so that
+ * their work overlaps on the GPU.  The first call with a given item list
+ * captures the whole fork/join into a CUDA graph; later calls with an
+ * identical list (same models, pointers and sizes) replay it with a single
+ * graph launch on the caller's stream.  Asynchronous: outputs are ready when
+ * the caller's stream reaches the launch. */
+typedef struct gwn_batch_s* gwn_batch;
+
+typedef struct {
+    gwn_model model;
+    const void* points;    /* device, n x dim, points_dtype (GWN_F32 or GWN_F64) */
+    int32_t points_dtype;
+    size_t n;              /* may be 0 (item skipped) */
+    double* out_w;         /* device, n values */
+    int32_t* out_label;    /* device, n, nullable */
+    uint32_t* out_status;  /* device, n, nullable (GWN_QS_* bits) */
+} gwn_query_item;
+
+/* A batch plan with n_streams streams (1..32), each owning a query workspace
+ * sized for the largest model it has seen; on `device` (-1 = current).
+ * Errors: INVALID_ARG, CUDA, OOM. */
+gwn_status gwn_batch_create(int32_t n_streams, int32_t device, gwn_batch* out);
+
+/* Enqueue the items on `stream` (cudaStream_t or NULL).  Models must have been
+ * built on the plan's device and must outlive the plan's captured graph (the
+ * next call with other items, or gwn_batch_release).  Errors: INVALID_ARG (bad
+ * item), OOM (workspaces), CUDA (capture or launch). */
+gwn_status gwn_query_batch(gwn_batch batch, const gwn_query_item* items, size_t n_items, void* stream);
+
+/* Graph launches so far, graph captures so far, bytes of the stream workspaces. */
+gwn_status gwn_batch_info(gwn_batch batch, int64_t* graph_launches, int64_t* captures, int64_t* workspace_bytes);
+
+/* Wait for the plan's streams and free it.  NULL is a no-op. */
+gwn_status gwn_batch_release(gwn_batch batch);
 
 /* ---------------------------------------------------------------- serving
  * A request loop over device-resident models with continuous batching (the

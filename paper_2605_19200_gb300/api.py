@@ -75,6 +75,12 @@ class gwn_server_stats(ctypes.Structure):
                 ("budget_used_bytes", ctypes.c_int64)]
 
 
+class gwn_query_item(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_void_p), ("points", ctypes.c_void_p), ("points_dtype", ctypes.c_int32),
+                ("n", ctypes.c_size_t), ("out_w", ctypes.c_void_p), ("out_label", ctypes.c_void_p),
+                ("out_status", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "gwn_default_build_opts": (None, [ctypes.POINTER(gwn_build_opts)]),
@@ -89,6 +95,11 @@ _SIGS = {
     "gwn_model_leaves": (ctypes.c_int, [_P, _P, _P]),
     "gwn_model_tree": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gwn_release": (ctypes.c_int, [_P]),
+    "gwn_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "gwn_query_batch": (ctypes.c_int, [_P, ctypes.POINTER(gwn_query_item), ctypes.c_size_t, _P]),
+    "gwn_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "gwn_batch_release": (ctypes.c_int, [_P]),
     "gwn_default_serve_opts": (None, [ctypes.POINTER(gwn_serve_opts)]),
     "gwn_serve_create": (ctypes.c_int, [ctypes.POINTER(gwn_serve_opts), ctypes.POINTER(_P)]),
     "gwn_serve_add_model": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
@@ -406,6 +417,63 @@ class Server:
     def close(self):
         if self.handle is not None and self.handle.value:
             _check(lib().gwn_serve_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """gwn_query_batch: many models and point sets in one (graph) launch."""
+
+    def __init__(self, n_streams: int = 4, device: int = -1):
+        h = ctypes.c_void_p()
+        _check(lib().gwn_batch_create(int(n_streams), int(device), ctypes.byref(h)))
+        self.handle = h
+        self._items = None
+        self._keep = None
+
+    def query(self, models, points, outs, stream=None):
+        """models: list of Model; points: list of CUDA tensors (n x dim, float32
+        or float64); outs: list of (w float64, label int32 or None, status int32
+        or None) CUDA tensors.  Enqueues on `stream`; returns outs."""
+        n = len(models)
+        if not (len(points) == n and len(outs) == n):
+            raise ValueError("models, points and outs must have the same length")
+        arr = (gwn_query_item * n)()
+        for k, (m, p, o) in enumerate(zip(models, points, outs)):
+            w, lab, st = o
+            if str(p.dtype) not in ("torch.float32", "torch.float64") or not p.is_contiguous():
+                raise TypeError("points must be contiguous float32 or float64 tensors")
+            if p.dim() != 2 or p.shape[1] != m.dim:
+                raise ValueError("points must be (n, dim)")
+            if str(w.dtype) != "torch.float64" or w.shape[0] < p.shape[0]:
+                raise TypeError("out w must be float64 with n entries")
+            for t in (lab, st):
+                if t is not None and (t.element_size() != 4 or t.shape[0] < p.shape[0]):
+                    raise TypeError("label and status outputs must be 32-bit with n entries")
+            arr[k].model = m.handle.value
+            arr[k].points = p.data_ptr()
+            arr[k].points_dtype = F32 if str(p.dtype).endswith("float32") else F64
+            arr[k].n = p.shape[0]
+            arr[k].out_w = w.data_ptr()
+            arr[k].out_label = lab.data_ptr() if lab is not None else None
+            arr[k].out_status = st.data_ptr() if st is not None else None
+        self._keep = (list(models), list(points), list(outs))
+        _check(lib().gwn_query_batch(self.handle, arr, n, _stream_handle(stream)))
+        return outs
+
+    def info(self) -> dict:
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().gwn_batch_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"graph_launches": a.value, "captures": b.value, "workspace_bytes": c.value}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gwn_batch_release(self.handle))
         self.handle = None
 
     def __del__(self):

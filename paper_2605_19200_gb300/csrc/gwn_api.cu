@@ -111,36 +111,42 @@ gwn_status init_constants(int dev) {
         bin[a][0] = bin[a][a] = 1.f;
         for (int b = 1; b < a; ++b) bin[a][b] = bin[a - 1][b - 1] + bin[a - 1][b];
     }
-    double x[8], w[8];
-    for (int i = 0; i < 8; ++i) {
-        double z = std::cos(M_PI * (i + 0.75) / 8.5), pp = 1;
-        for (int it = 0; it < 100; ++it) {
-            double p1 = 1, p2 = 0;
-            for (int j = 1; j <= 8; ++j) {
-                double p3 = p2;
-                p2 = p1;
-                p1 = ((2.0 * j - 1) * z * p2 - (j - 1.0) * p3) / j;
+    // n-point Gauss-Legendre nodes and weights on [0, 1]: Newton's method on the
+    // Legendre polynomial P_n from the standard cosine initial guesses
+    auto gauss = [](int n, double* x, double* w) {
+        for (int i = 0; i < n; ++i) {
+            double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 1;
+            for (int it = 0; it < 100; ++it) {
+                double p1 = 1, p2 = 0;
+                for (int j = 1; j <= n; ++j) {
+                    double p3 = p2;
+                    p2 = p1;
+                    p1 = ((2.0 * j - 1) * z * p2 - (j - 1.0) * p3) / j;
+                }
+                pp = n * (z * p1 - p2) / (z * z - 1);
+                double dz = p1 / pp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-16) break;
             }
-            pp = 8 * (z * p1 - p2) / (z * z - 1);
-            double dz = p1 / pp;
-            z -= dz;
-            if (std::fabs(dz) < 1e-16) break;
+            x[i] = 0.5 * (1 - z);
+            w[i] = 1.0 / ((1 - z * z) * pp * pp);
         }
-        x[i] = 0.5 * (1 - z);
-        w[i] = 1.0 / ((1 - z * z) * pp * pp);
-    }
-    float xf[8], wf[8];
-    for (int i = 0; i < 8; ++i) {
-        xf[i] = (float)x[i];
-        wf[i] = (float)w[i];
+    };
+    double x[8], w[8], x6[6], w6[6];
+    gauss(8, x, w);
+    gauss(6, x6, w6);
+    float xf[6], wf[6];
+    for (int i = 0; i < 6; ++i) {
+        xf[i] = (float)x6[i];
+        wf[i] = (float)w6[i];
     }
     std::memcpy(h_binom, bin, sizeof(bin));
     std::memcpy(h_glx8, x, sizeof(x));
     std::memcpy(h_glw8, w, sizeof(w));
-    std::memcpy(h_glx8f, xf, sizeof(xf));
-    std::memcpy(h_glw8f, wf, sizeof(wf));
-    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx8f, xf, sizeof(xf)));
-    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw8f, wf, sizeof(wf)));
+    std::memcpy(h_glx6f, xf, sizeof(xf));
+    std::memcpy(h_glw6f, wf, sizeof(wf));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx6f, xf, sizeof(xf)));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw6f, wf, sizeof(wf)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx8, x, sizeof(x)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw8, w, sizeof(w)));
@@ -383,6 +389,13 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
 
 constexpr size_t kChunk = (size_t)1 << 19;  // points per pass of the query pipeline
 
+// beta of the FP64 repair when the build leaves it automatic: the exact sum over
+// every leaf for small models, else the traversal at 3 beta, whose order-2
+// remainder is 3^-4 = 1/81 of the bulk's (Eq. 3's remainder falls like beta^-4)
+double auto_beta_repair(const gwn_model_s* m, double beta) {
+    return m->host.n_leaves <= 512 ? 0.0 : 3.0 * beta;
+}
+
 gwn_status ensure_workspace(gwn_model_s* m, size_t n, size_t stage_bytes) {
     n = std::min(n, kChunk);
     if (n > m->ws_n || !m->ws_mem) {
@@ -428,7 +441,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
     double beta_leaf = qo.beta_leaf > 0 ? qo.beta_leaf : (m->opts.beta_leaf > 0 ? m->opts.beta_leaf : beta);
     p.beta2_leaf = (float)(beta_leaf * beta_leaf);
     double br = m->opts.beta_repair;
-    if (br < 0) br = m->host.n_leaves <= 4096 ? 0.0 : 2.0 * beta;  // automatic choice
+    if (br < 0) br = auto_beta_repair(m, beta);
     p.beta2_repair = br > 0 ? br * br : 0.0;
     p.band = (float)m->opts.repair_band;
     p.mode = qo.mode;
@@ -917,7 +930,7 @@ extern "C" gwn_status gwn_query_noalloc(gwn_model m, const void* points, int32_t
     p.beta2 = (float)(beta * beta);
     p.beta2_leaf = (float)(beta_leaf * beta_leaf);
     double br = m->opts.beta_repair;
-    if (br < 0) br = m->host.n_leaves <= 4096 ? 0.0 : 2.0 * beta;
+    if (br < 0) br = auto_beta_repair(m, beta);
     p.beta2_repair = br > 0 ? br * br : 0.0;
     p.band = (float)m->opts.repair_band;
     p.mode = GWN_MODE_BVH;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libgwn.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["gwn_api.cu", "gwn_serve.cu"]
+CU_SOURCES = ["gwn_api.cu", "gwn_serve.cu", "gwn_batch.cu"]
 CPP_SOURCES = ["build.cpp", "build3d.cpp"]
 
 

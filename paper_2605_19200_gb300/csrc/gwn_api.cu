@@ -132,21 +132,21 @@ gwn_status init_constants(int dev) {
             w[i] = 1.0 / ((1 - z * z) * pp * pp);
         }
     };
-    double x[8], w[8], x6[6], w6[6];
+    double x[8], w[8], x4[4], w4[4];
     gauss(8, x, w);
-    gauss(6, x6, w6);
-    float xf[6], wf[6];
-    for (int i = 0; i < 6; ++i) {
-        xf[i] = (float)x6[i];
-        wf[i] = (float)w6[i];
+    gauss(4, x4, w4);
+    float xf[4], wf[4];
+    for (int i = 0; i < 4; ++i) {
+        xf[i] = (float)x4[i];
+        wf[i] = (float)w4[i];
     }
     std::memcpy(h_binom, bin, sizeof(bin));
     std::memcpy(h_glx8, x, sizeof(x));
     std::memcpy(h_glw8, w, sizeof(w));
-    std::memcpy(h_glx6f, xf, sizeof(xf));
-    std::memcpy(h_glw6f, wf, sizeof(wf));
-    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx6f, xf, sizeof(xf)));
-    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw6f, wf, sizeof(wf)));
+    std::memcpy(h_glx4f, xf, sizeof(xf));
+    std::memcpy(h_glw4f, wf, sizeof(wf));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx4f, xf, sizeof(xf)));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw4f, wf, sizeof(wf)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx8, x, sizeof(x)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw8, w, sizeof(w)));
@@ -443,6 +443,9 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
     double br = m->opts.beta_repair;
     if (br < 0) br = auto_beta_repair(m, beta);
     p.beta2_repair = br > 0 ? br * br : 0.0;
+    // the repair's leaves keep the bulk's ratio beta_leaf / beta
+    const double brl = br * beta_leaf / beta;
+    p.beta2_repair_leaf = brl > 0 ? brl * brl : 0.0;
     p.band = (float)m->opts.repair_band;
     p.mode = qo.mode;
     p.precision = qo.precision >= 0 ? qo.precision : m->opts.precision;
@@ -554,9 +557,10 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
             k_rtrav_warp<2><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, p.beta2_repair, ws.rlist, ws, out_w,
                                                              out_label, out_status);
         } else {
-            const double b2r = p.mode == GWN_MODE_DIRECT ? 0.0 : p.beta2_repair;
-            k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, b2r, ws.rlist, ws, out_w,
-                                                             out_label, out_status);
+            const bool direct = p.mode == GWN_MODE_DIRECT;
+            k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, direct ? 0.0 : p.beta2_repair,
+                                                             ws.rlist, ws, out_w, out_label, out_status,
+                                                             direct ? 0.0 : p.beta2_repair_leaf);
             k_rpairs3_warp<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.rlist, ws);
             k_rfinish<<<(unsigned)(sms * 2), B, 0, st>>>(ws.rlist, ws, out_w, out_label, out_status);
         }

@@ -134,6 +134,7 @@ struct QueryParams {
     float beta2;               // beta^2 of the FP32 pass (internal nodes)
     float beta2_leaf;          // beta^2 of the leaves' own far test (3D)
     double beta2_repair;       // beta^2 of the FP64 repair pass; <= 0: direct sum
+    double beta2_repair_leaf;  // beta^2 of the repair's leaf far test (3D)
     float band;                // repair band around half-integers
     int mode;                  // GWN_MODE_*
     int precision;             // GWN_PREC_*

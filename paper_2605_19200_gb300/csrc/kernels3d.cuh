@@ -37,11 +37,12 @@ constexpr int kLevel32 = 10;
 constexpr int kLevel64 = 30;
 // panel length / distance-to-q bound of the 8-point rule: the quadrature error
 // of an analytic integrand decays like rho^-16 with rho the Bernstein-ellipse
-// parameter, ~3.0 at 1.5.  The FP32 bulk uses 1.5, and so does the FP64 near
-// band that completes it (there FP64 is needed for the geometry, not for the
-// quadrature).  The repair uses 1.0 (measured ~1e-7 against the oracle) and
-// the all-FP64 precision mode 0.5 (~1e-8).
-constexpr float kRatio32 = 1.5f;
+// parameter, ~3.0 at 1.5 and ~6 at 0.75.  The FP32 bulk takes 4-point panels
+// at 0.75 (error ~6^-8); the FP64 near band that completes it 8-point panels
+// at 1.5 (FP64 is needed there for the geometry, not for the quadrature); the
+// repair 1.0 (measured ~1e-7 against the oracle); the all-FP64 precision mode
+// 0.5 (~1e-8).
+constexpr float kRatio32 = 0.75f;
 constexpr double kRatio64Band = 1.5;
 constexpr double kRatio64Repair = 1.0;
 constexpr double kRatio64Exact = 0.5;
@@ -51,23 +52,23 @@ constexpr double kRatio64Exact = 0.5;
 __constant__ float c_binom[kMaxC3Deg + 1][kMaxC3Deg + 1];
 __constant__ double c_glx8[8];
 __constant__ double c_glw8[8];
-__constant__ float c_glx6f[6];
-__constant__ float c_glw6f[6];
+__constant__ float c_glx4f[4];
+__constant__ float c_glw4f[4];
 static float h_binom[kMaxC3Deg + 1][kMaxC3Deg + 1];
 static double h_glx8[8], h_glw8[8];
-static float h_glx6f[6], h_glw6f[6];
+static float h_glx4f[4], h_glw4f[4];
 #if defined(__CUDA_ARCH__)
 #define GWN_BINOM(d, i) c_binom[d][i]
 #define GWN_GLX(k) c_glx8[k]
 #define GWN_GLW(k) c_glw8[k]
-#define GWN_GLXF(k) c_glx6f[k]
-#define GWN_GLWF(k) c_glw6f[k]
+#define GWN_GLXF(k) c_glx4f[k]
+#define GWN_GLWF(k) c_glw4f[k]
 #else
 #define GWN_BINOM(d, i) h_binom[d][i]
 #define GWN_GLX(k) h_glx8[k]
 #define GWN_GLW(k) h_glw8[k]
-#define GWN_GLXF(k) h_glx6f[k]
-#define GWN_GLWF(k) h_glw6f[k]
+#define GWN_GLXF(k) h_glx4f[k]
+#define GWN_GLWF(k) h_glw4f[k]
 #endif
 
 // accessors of one leaf's geometry, in FP32 (relative to the leaf centre) or FP64 (absolute)
@@ -170,16 +171,19 @@ GWN_HD inline void bern4_fixed(const G& g0, T t, T X[4], T dX[4]) {
     }
 }
 
-// Gauss-Legendre rules on [0, 1] of the panels: 6 points in FP32 (relative
-// error ~rho^-12 ~ 2e-6 per panel at the FP32 panel ratio), 8 in FP64
+// Gauss-Legendre rules on [0, 1] of the panels: 4 points in FP32 (relative
+// error ~rho^-8 ~ 6e-7 per panel at the FP32 panel ratio 0.75, rho ~ 6), 8 in
+// FP64; span = fraction of the panel between the first and the last node
 template <typename T> struct Gl8;
 template <> struct Gl8<float> {
-    static constexpr int K = 6;
+    static constexpr int K = 4;
+    static constexpr float span_inv = 1.17f;  // nodes span 86 % of the panel
     static GWN_HD inline float x(int k) { return GWN_GLXF(k); }
     static GWN_HD inline float w(int k) { return GWN_GLWF(k); }
 };
 template <> struct Gl8<double> {
     static constexpr int K = 8;
+    static constexpr double span_inv = 1.1;  // nodes span 96 % of the panel
     static GWN_HD inline double x(int k) { return GWN_GLX(k); }
     static GWN_HD inline double w(int k) { return GWN_GLW(k); }
 };
@@ -253,8 +257,7 @@ GWN_HD T panel_subtree_d(const G& g, int D, const T q[3], const T s[3], int leve
             wl->v[kWorkGlNodes] += Gl8<T>::K;
             wl->v[kWorkGlDeg] += (unsigned long long)Gl8<T>::K * (unsigned long long)D;
         }
-        // the nodes span 93% (6 points) or 96% (8 points) of the panel
-        len *= T(1.1);
+        len *= T(Gl8<T>::span_inv);
         bool refine = len * len > ratio2 * dmin2;
         if (refine && level < maxlevel) {
             ++level;
@@ -289,6 +292,8 @@ GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int 
                              WorkLocal* wl = nullptr) {
     return panel_subtree<T>(g, D, q, s, 0, 0u, maxlevel, ratio, deep, wl);
 }
+
+
 
 // S, S_u, S_v of the leaf's bicubic net at local (u, v)
 template <typename T, typename G>

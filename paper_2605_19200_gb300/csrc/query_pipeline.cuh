@@ -136,18 +136,34 @@ __device__ __forceinline__ void flush_pairs(int2* local, int cnt, Workspace ws, 
     }
 }
 
-// traversal with deferred 3D leaves; every thread of the grid reaches the
-// warp-wide flushes (out-of-range threads take part with no pairs)
+// traversal with deferred 3D leaves, one packet per warp: the 32 queries of a
+// warp (neighbours in the binned order) walk the tree together.  The warp
+// holds one node and the mask of its lanes that still need that subtree; each
+// lane applies the far test, far lanes add the node's Taylor term, and the
+// children are visited (the second one through a warp stack in shared memory)
+// with the mask of the lanes for which the node was near.  Node and moment
+// loads are then the same address for the whole warp, and lanes never wait on
+// each other's different branches.  Binned queries share most of their paths
+// (the union of a warp's visits is ~1.05x the longest single path), so the
+// packet costs little extra work.  Exact 3D leaves go to the pair list (warp-
+// wide flushes); every thread of the grid reaches them (lanes past the end of
+// the list take part with an empty mask).
 // n_dev != nullptr: the point list `perm` holds *n_dev entries (a later round
 // over the points whose pairs overflowed; their indices go to `olist_out`)
+constexpr int kPacketStack = 96;  // entries per warp
+
 __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int dtype, int n, const int* perm,
                                                float beta2, float beta2l, Workspace ws, unsigned long long* work,
                                                const int* n_dev, int* olist_out) {
+    __shared__ int2 sstk[4][kPacketStack];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int2* stk = sstk[threadIdx.x >> 5];
     WorkLocal wl = {};
     if (n_dev) n = *n_dev;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (n_dev && blockIdx.x * blockDim.x >= n) return;  // whole block past the list
-    bool active = i < n;
+    const bool active = i < n;
     int qi = active ? (perm ? perm[i] : i) : 0;
     float q[3] = {0, 0, 0};
     if (active) load_point_f(pts, dtype, 3, qi, q);
@@ -155,50 +171,63 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
     uint32_t st = 0;
     int2 local[kPairLocal];
     int cnt = 0;
-    int stack[kStack32];
-    int sp = 0;
-    int node = active ? t.root : 0;
-    bool running = active;
-    while (__any_sync(0xffffffffu, running)) {
-        if (running) {
-            bool pop = true;
-            if (node < 0) {
-                int li = ~node;
-                float4 h = GWN_LDG(t.lhdr + li);
-                float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
-                if (work) wl.v[kWorkLeafTests] += 1;
-                if (t.leaf_far && rx * rx + ry * ry + rz * rz > beta2l * h.w) {
-                    if (work) wl.v[kWorkFar] += 1;
-                    w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
-                } else {
-                    local[cnt++] = make_int2(qi, li);
-                }
-            } else {
-                float4 h = GWN_LDG(t.hdr + node);
-                float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
-                if (work) wl.v[kWorkNodes] += 1;
-                if (rx * rx + ry * ry + rz * rz > beta2 * h.w) {
-                    if (work) wl.v[kWorkFar] += 1;
-                    w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz);
-                } else {
-                    int2 ch = GWN_LDG(t.child + node);
-                    if (sp < kStack32) stack[sp++] = ch.y; else st |= GWN_QS_STACK_OVERFLOW;
-                    node = ch.x;
-                    pop = false;
-                }
+    int sp = 0;                        // warp-uniform
+    int node = t.root;                 // warp-uniform
+    unsigned mask = __ballot_sync(full, active);
+    while (mask) {
+        const bool mine = (mask >> lane) & 1u;
+        bool descend = false;
+        if (node < 0) {
+            const int li = ~node;
+            const float4 h = GWN_LDG(t.lhdr + li);
+            const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
+            const bool far = mine && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2l * h.w;
+            if (work && mine) wl.v[kWorkLeafTests] += 1;
+            if (far) {
+                if (work) wl.v[kWorkFar] += 1;
+                w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
+            } else if (mine) {
+                local[cnt++] = make_int2(qi, li);
             }
-            if (pop) {
-                if (sp == 0) running = false;
-                else node = stack[--sp];
+            // flush when any lane's buffer is full (warp-uniform decision)
+            if (__any_sync(full, cnt == kPairLocal)) {
+                flush_pairs(local, cnt, ws, st, full);
+                cnt = 0;
+            }
+        } else {
+            const float4 h = GWN_LDG(t.hdr + node);
+            const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
+            const bool far = mine && rx * rx + ry * ry + rz * rz > beta2 * h.w;
+            if (work && mine) wl.v[kWorkNodes] += 1;
+            if (far) {
+                if (work) wl.v[kWorkFar] += 1;
+                w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz);
+            }
+            const unsigned near = __ballot_sync(full, mine && !far);
+            if (near) {
+                const int2 ch = GWN_LDG(t.child + node);
+                if (sp < kPacketStack) {
+                    if (lane == 0) stk[sp] = make_int2(ch.y, (int)near);
+                    ++sp;
+                } else if ((near >> lane) & 1u) {
+                    st |= GWN_QS_STACK_OVERFLOW;  // the second subtree is dropped for these lanes
+                }
+                __syncwarp();
+                node = ch.x;
+                mask = near;
+                descend = true;
             }
         }
-        // flush when any lane's buffer is full (warp-uniform decision)
-        if (__any_sync(0xffffffffu, cnt == kPairLocal)) {
-            flush_pairs(local, cnt, ws, st, 0xffffffffu);
-            cnt = 0;
+        if (!descend) {
+            if (sp == 0) break;
+            --sp;
+            const int2 e = stk[sp];
+            node = e.x;
+            mask = (unsigned)e.y;
+            __syncwarp();
         }
     }
-    flush_pairs(local, cnt, ws, st, 0xffffffffu);
+    flush_pairs(local, cnt, ws, st, full);
     if (active) {
         ws.wacc[qi] = w;
         ws.st[qi] = st;
@@ -494,7 +523,9 @@ constexpr int kRepairWarps = 4;  // warps per block
 template <int DIM>
 __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, const void* pts, int dtype, double beta2r,
                                                                   const int* rlist, Workspace ws, double* out_w,
-                                                                  int* out_label, uint32_t* out_status) {
+                                                                  int* out_label, uint32_t* out_status,
+                                                                  double beta2rl = -1.0) {
+    if (beta2rl < 0) beta2rl = beta2r;  // leaves' far test (3D): default the nodes' factor
     __shared__ int sstack[kRepairWarps][kWarpStack];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kRepairWarps + wid;
@@ -530,7 +561,7 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
                     } else {
                         const double* h = t.lhdr64 + (size_t)li * 4;
                         double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
-                        if (beta2r > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2r * h[3]) {
+                        if (beta2rl > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2rl * h[3]) {
                             acc += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
                         } else {
                             int slot = atomicAdd(&ws.counters[4], 1);

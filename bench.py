@@ -40,6 +40,8 @@ import numpy as np
 BETA = 0.0              # 0: the build's autotuner picks beta and beta_leaf per model for max |dGWN| <= 1e-4
 DIRECT_SAMPLE = 40960   # queries per model for the plain direct-sum comparison (fills the GPU)
 ORACLE_SAMPLE = 2       # queries per model for the CPU oracle
+WORKLOAD_NAME = ("cad16: 16 models of trimmed bicubic rational patches (box/cylinder unions), "
+                 "queries uniform in each model's box")
 PAIR_EVAL_DRAM_BYTES_PER_PAIR = 10.5  # ncu dram__bytes_read + dram__bytes_write of k_pair_eval per pair
 
 
@@ -160,8 +162,9 @@ def reference_arm(args):
             "unit": "queries/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "cad16: 16 models, 1k-40k trimmed bicubic rational patches, 64k-4M queries each",
-                       "sample": sample},
+            "config": {"workload": WORKLOAD_NAME, "models": len(workload),
+                       "patches": sum(len(p) for p, _ in workload),
+                       "queries_per_step": sum(q.shape[0] for _, q in workload), "sample": sample},
             "cpu_baseline": {"value": val, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -446,8 +449,7 @@ def main():
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "cad16: 16 models of trimmed bicubic rational patches (box/cylinder unions), "
-                               "queries uniform in each model's box",
+        "config": {"workload": WORKLOAD_NAME,
                    "models": len(models), "patches": n_patches, "leaves": n_leaves, "queries_per_step": total_q,
                    "beta": "autotuned" if args.beta == 0 else args.beta, "beta_per_model": tuned,
                    "tolerance": 1e-4, "order": 2, "precision": "fp32 bulk + fp64 repair",

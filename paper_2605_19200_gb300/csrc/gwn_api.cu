@@ -145,6 +145,10 @@ gwn_status init_constants(int dev) {
     std::memcpy(h_glw8, w, sizeof(w));
     std::memcpy(h_glx4f, xf, sizeof(xf));
     std::memcpy(h_glw4f, wf, sizeof(wf));
+    std::memcpy(h_glx4d, x4, sizeof(x4));
+    std::memcpy(h_glw4d, w4, sizeof(w4));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx4d, x4, sizeof(x4)));
+    GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw4d, w4, sizeof(w4)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glx4f, xf, sizeof(xf)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_glw4f, wf, sizeof(wf)));
     GWN_CUDA_TRY(cudaMemcpyToSymbol(c_binom, bin, sizeof(bin)));

@@ -46,6 +46,10 @@ constexpr float kRatio32 = 0.75f;
 constexpr double kRatio64Band = 1.5;
 constexpr double kRatio64Repair = 1.0;
 constexpr double kRatio64Exact = 0.5;
+// the warp evaluator (leaf3_warp64<4>) takes 4-point panels at half these ratios,
+// which keeps the same Bernstein-ellipse margin per panel with half the nodes
+constexpr double kRatio64BandW4 = 0.75;
+constexpr double kRatio64RepairW4 = 0.5;
 
 // binomial coefficients and the 8-point Gauss-Legendre rule on [0, 1]: device
 // constant memory, with host mirrors for host-side execution
@@ -54,21 +58,28 @@ __constant__ double c_glx8[8];
 __constant__ double c_glw8[8];
 __constant__ float c_glx4f[4];
 __constant__ float c_glw4f[4];
+__constant__ double c_glx4d[4];
+__constant__ double c_glw4d[4];
 static float h_binom[kMaxC3Deg + 1][kMaxC3Deg + 1];
 static double h_glx8[8], h_glw8[8];
 static float h_glx4f[4], h_glw4f[4];
+static double h_glx4d[4], h_glw4d[4];
 #if defined(__CUDA_ARCH__)
 #define GWN_BINOM(d, i) c_binom[d][i]
 #define GWN_GLX(k) c_glx8[k]
 #define GWN_GLW(k) c_glw8[k]
 #define GWN_GLXF(k) c_glx4f[k]
 #define GWN_GLWF(k) c_glw4f[k]
+#define GWN_GLX4D(k) c_glx4d[k]
+#define GWN_GLW4D(k) c_glw4d[k]
 #else
 #define GWN_BINOM(d, i) h_binom[d][i]
 #define GWN_GLX(k) h_glx8[k]
 #define GWN_GLW(k) h_glw8[k]
 #define GWN_GLXF(k) h_glx4f[k]
 #define GWN_GLWF(k) h_glw4f[k]
+#define GWN_GLX4D(k) h_glx4d[k]
+#define GWN_GLW4D(k) h_glw4d[k]
 #endif
 
 // accessors of one leaf's geometry, in FP32 (relative to the leaf centre) or FP64 (absolute)
@@ -241,7 +252,8 @@ GWN_HD T panel_subtree_d(const G& g, int D, const T q[3], const T s[3], int leve
         const T a = T(idx) * h;
         T psum = 0, dmin2 = T(1e30), len = 0;
         T px = 0, py = 0, pz = 0;
-#pragma unroll 1
+        // FP32 with a fixed degree: nodes unrolled by two (independent evaluations, ILP)
+#pragma unroll(DF > 0 && sizeof(T) == 4 ? 2 : 1)
         for (int k = 0; k < Gl8<T>::K; ++k) {
             T x[3], dm2;
             T f = gl_node<DF, T>(g, D, a + h * Gl8<T>::x(k), q, s, x, &dm2);
@@ -545,8 +557,8 @@ GWN_HD inline float leaf3_eval32(const DevTree& t, int li, float qx, float qy, f
 // Gauss-Legendre nodes one after another at FP64 latency, and such a single
 // pair bounds the duration of its whole launch.  Here lane 0 does the crossing
 // test, then the warp works through the adaptive panels of all boundary curves
-// as a shared list (in shared memory, `stk`, kQuadStack entries): four panels
-// per step, one Gauss-Legendre node per lane, the 8 lanes of a panel reducing
+// as a shared list (in shared memory, `stk`, kQuadStack entries): 32 / K panels
+// per step, one Gauss-Legendre node per lane, the K lanes of a panel reducing
 // its sum, distance and length with shuffles.  A panel that fails the length
 // test pushes its two halves; when the list is full its group's leader
 // integrates the panel's subtree alone.  Same arithmetic as leaf3_core<double>
@@ -555,10 +567,13 @@ GWN_HD inline float leaf3_eval32(const DevTree& t, int li, float qx, float qy, f
 constexpr int kQuadStack = 256;
 
 #if defined(__CUDACC__)
+template <int K>
 __device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3], double ratio, int maxlevel, int2* stk,
                                     double* out) {
+    static_assert(K == 4 || K == 8, "4 or 8 nodes per panel");
+    constexpr int kPanels = 32 / K;                    // panels per step
     const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, grp = lane >> 3, k = lane & 7;
+    const int lane = threadIdx.x & 31, grp = lane / K, k = lane % K;
     const Leaf3Info I = t.leaf3[li];
     const Geo64 g{t.net3_64 + (size_t)li * 64, nullptr};
     const double nrm[3] = {(double)I.nrm[0], (double)I.nrm[1], (double)I.nrm[2]};
@@ -592,7 +607,7 @@ __device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3],
         next_curve += add;
         __syncwarp();
         if (sp == 0) break;
-        const int take = min(sp, 4);
+        const int take = min(sp, kPanels);
         int2 task = make_int2(-1, 0);
         if (grp < take) task = stk[sp - 1 - grp];
         sp -= take;
@@ -610,7 +625,8 @@ __device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3],
             ci = t.c3[I.c3_off + cidx];
             gc.pts = t.c3pts64 + (size_t)ci.ctrl_off * 4;
             h = 1.0 / double(1u << level);
-            f = gl_node_any<double>(gc, ci.deg, double(idx) * h + h * Gl8<double>::x(k), q, s, x, &dm2);
+            const double xk = K == 8 ? Gl8<double>::x(k) : GWN_GLX4D(k);
+            f = gl_node_any<double>(gc, ci.deg, double(idx) * h + h * xk, q, s, x, &dm2);
         }
         const double p0 = __shfl_up_sync(full, x[0], 1), p1 = __shfl_up_sync(full, x[1], 1),
                      p2 = __shfl_up_sync(full, x[2], 1);
@@ -619,13 +635,13 @@ __device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3],
             const double e0 = x[0] - p0, e1 = x[1] - p1, e2 = x[2] - p2;
             seg = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
         }
-        double psum = act ? Gl8<double>::w(k) * f : 0.0;
-        for (int off = 1; off < 8; off <<= 1) {
+        double psum = act ? (K == 8 ? Gl8<double>::w(k) : GWN_GLW4D(k)) * f : 0.0;
+        for (int off = 1; off < K; off <<= 1) {
             psum += __shfl_xor_sync(full, psum, off);
             seg += __shfl_xor_sync(full, seg, off);
             dm2 = fmin(dm2, __shfl_xor_sync(full, dm2, off));
         }
-        const double len = seg * 1.1;  // the 8 nodes span ~96% of the panel
+        const double len = seg * (K == 8 ? 1.1 : 1.17);  // the nodes span 96 % (8) or 86 % (4) of the panel
         const bool refine = act && len * len > ratio2 * dm2;
         const bool split = refine && level < maxlevel;
         if (refine && !split) deep = true;

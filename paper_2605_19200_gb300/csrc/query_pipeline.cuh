@@ -312,6 +312,18 @@ __global__ void k_pair_eval64(DevTree t, const void* pts, int dtype, int npair64
     }
 }
 
+// 4-point FP64 panels are used for leaves whose boundary curves all have degree
+// <= 6 (pieces of degree 1 composed with the bicubic net); curves of higher
+// degree (rational trims) take 8-point panels, whose error does not depend on
+// how close the rational parametrisation's poles come to the panel
+__device__ __forceinline__ bool leaf_fits_w4(const DevTree& t, int li) {
+    const Leaf3Info I = t.leaf3[li];
+    int dmax = 0;
+    for (int c = threadIdx.x & 31; c < I.c3_cnt; c += 32) dmax = max(dmax, t.c3[I.c3_off + c].deg);
+    for (int off = 16; off > 0; off >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+    return dmax <= 6;
+}
+
 // the near band with one warp per pair (leaf3_warp64)
 __global__ void __launch_bounds__(128) k_pair_eval64_warp(DevTree t, const void* pts, int dtype, int npair64_cap,
                                                           const int* counters, const int2* pairs64, float* wacc,
@@ -330,7 +342,8 @@ __global__ void __launch_bounds__(128) k_pair_eval64_warp(DevTree t, const void*
             q[0] = (double)(float)p[0]; q[1] = (double)(float)p[1]; q[2] = (double)(float)p[2];
         }
         double v = 0;
-        const bool ok = leaf3_warp64(t, pr.y, q, kRatio64Band, kLevel64, sstk[wid], &v);
+        const bool ok = leaf_fits_w4(t, pr.y) ? leaf3_warp64<4>(t, pr.y, q, kRatio64BandW4, kLevel64, sstk[wid], &v)
+                                              : leaf3_warp64<8>(t, pr.y, q, kRatio64Band, kLevel64, sstk[wid], &v);
         if (lane == 0) {
             atomicAdd(&wacc[pr.x], ok ? (float)v : 0.f);
             if (!ok) atomicOr(&st[pr.x], GWN_QS_UNRESOLVED);
@@ -339,20 +352,76 @@ __global__ void __launch_bounds__(128) k_pair_eval64_warp(DevTree t, const void*
     }
 }
 
-// 2D traversal (leaves evaluated in place) in binned order
+// 2D traversal in binned order, one packet per warp as in k_trav3 (node + lane
+// mask, second children on a shared-memory warp stack); 2D leaves are
+// evaluated in place by the lanes that reach them (an exact 2D leaf costs a
+// chord angle, see leaf2_eval32)
 __global__ void __launch_bounds__(128) k_trav2(DevTree t, const void* pts, int dtype, int n, const int* perm,
                                                float beta2, Workspace ws, unsigned long long* work) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int qi = perm ? perm[i] : i;
-    float q[2];
-    load_point_f(pts, dtype, 2, qi, q);
-    uint32_t st = 0;
+    __shared__ int2 sstk[4][kPacketStack];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int2* stk = sstk[threadIdx.x >> 5];
     WorkLocal wl = {};
-    float w = query2_32(t, q[0], q[1], beta2, st, work ? &wl : nullptr);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < n;
+    const int qi = active ? (perm ? perm[i] : i) : 0;
+    float q[2] = {0, 0};
+    if (active) load_point_f(pts, dtype, 2, qi, q);
+    float w = 0.f;
+    uint32_t st = 0;
+    int sp = 0;                        // warp-uniform
+    int node = t.root;                 // warp-uniform
+    unsigned mask = __ballot_sync(full, active);
+    while (mask) {
+        const bool mine = (mask >> lane) & 1u;
+        bool descend = false;
+        if (node < 0) {
+            if (mine) {
+                if (work) wl.v[kWorkLeaves] += 1;
+                w += leaf2_eval32(t, ~node, q[0], q[1], st);
+            }
+        } else {
+            const float4 h = GWN_LDG(t.hdr + node);
+            const float rx = h.x - q[0], ry = h.y - q[1];
+            const bool far = mine && rx * rx + ry * ry > beta2 * h.w;
+            if (work && mine) wl.v[kWorkNodes] += 1;
+            if (far) {
+                if (work) wl.v[kWorkFar] += 1;
+                const float4* M = t.mom + (size_t)node * kMom2Vec;
+                const float4 a = GWN_LDG(M), b = GWN_LDG(M + 1), c = GWN_LDG(M + 2);
+                const float f[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+                w += far2_eval<float>(f, rx, ry);
+            }
+            const unsigned near = __ballot_sync(full, mine && !far);
+            if (near) {
+                const int2 ch = GWN_LDG(t.child + node);
+                if (sp < kPacketStack) {
+                    if (lane == 0) stk[sp] = make_int2(ch.y, (int)near);
+                    ++sp;
+                } else if ((near >> lane) & 1u) {
+                    st |= GWN_QS_STACK_OVERFLOW;  // the second subtree is dropped for these lanes
+                }
+                __syncwarp();
+                node = ch.x;
+                mask = near;
+                descend = true;
+            }
+        }
+        if (!descend) {
+            if (sp == 0) break;
+            --sp;
+            const int2 e = stk[sp];
+            node = e.x;
+            mask = (unsigned)e.y;
+            __syncwarp();
+        }
+    }
+    if (active) {
+        ws.wacc[qi] = w;
+        ws.st[qi] = st;
+    }
     if (work) flush_work(wl, work);
-    ws.wacc[qi] = w;
-    ws.st[qi] = st;
 }
 
 __global__ void k_finish(int n, const float* wacc, const uint32_t* stv, int precision, float band, double* out_w,
@@ -470,7 +539,8 @@ __global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts
             q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
         }
         double v = 0;
-        const bool ok = leaf3_warp64(t, pr.y, q, kRatio64Repair, kLevel64, sstk[wid], &v);
+        const bool ok = leaf_fits_w4(t, pr.y) ? leaf3_warp64<4>(t, pr.y, q, kRatio64RepairW4, kLevel64, sstk[wid], &v)
+                                              : leaf3_warp64<8>(t, pr.y, q, kRatio64Repair, kLevel64, sstk[wid], &v);
         if (lane == 0) {
             if (ok) atomicAdd(&ws.rw[pr.x], v);
             else atomicOr(&ws.st[qi], GWN_QS_UNRESOLVED);

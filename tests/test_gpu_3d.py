@@ -144,14 +144,21 @@ def test_autotuned_beta_meets_tolerance(oracle_lib):
     assert np.max(np.abs(w[ok] - w_ref[ok])) <= 1e-4
 
 
-@pytest.mark.parametrize("beta_repair,tol", [(0.0, 1e-6), (12.0, 1e-4)])
-def test_repair_of_most_points(oracle_lib, beta_repair, tol):
-    """The trimmed sphere is an open surface, so its GWN takes every value in
-    (0, 1); a repair band of 0.4999 then sends almost every query through the
-    FP64 repair (warp traversal and the FP64 pair list, one warp per pair).
-    With beta_repair = 0 the repair is the exact sum over every leaf, held to
-    1e-6; with beta_repair = 12 its far field is Taylor, held to 1e-4."""
-    patches, q = configs.sphere_3d(n_queries=3000)
+@pytest.mark.parametrize("shape,beta_repair,tol", [("sphere", 0.0, 1e-6), ("sphere", 12.0, 1e-4),
+                                                    ("cad_open", 0.0, 1e-6)])
+def test_repair_of_most_points(oracle_lib, shape, beta_repair, tol):
+    """The trimmed sphere (disc trims: rational boundary curves of degree 12) and
+    every other patch of a CAD solid (polygon trims: degree 6) are open surfaces,
+    so their GWN takes every value in (0, 1); a repair band of 0.4999 then sends
+    almost every query through the FP64 repair (warp traversal and the FP64 pair
+    list, one warp per pair, 8- or 4-point panels by degree).  With
+    beta_repair = 0 the repair is the exact sum over every leaf, held to 1e-6;
+    with beta_repair = 12 its far field is Taylor, held to 1e-4."""
+    if shape == "sphere":
+        patches, q = configs.sphere_3d(n_queries=3000)
+    else:
+        patches, q = configs.cad_3d(2468, 400, 3000)
+        patches = patches[::2]
     sel = q[:500]
     w_ref, fl = oracle_lib.gwn3d(patches, sel, near_thr=1e-6 * _diag(patches))
     ok = np.isfinite(w_ref)

@@ -1,0 +1,42 @@
+"""GPU tests of the parameter sweeps (Section 4.2: Taylor order and beta).
+
+For a cluster of fixed size, the remainder of Eq. 3's expansion after order p
+falls like beta^-(p + 2) in 2D and beta^-(p + 3) in 3D, so at fixed order the
+error must shrink as beta grows, and order 2 must be well below orders 0 and 1.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2605_19200_gb300 as gwn
+from paper_2605_19200_gb300 import sweep as S
+from synth import configs
+
+
+def _rows(rows, **sel):
+    return [r for r in rows if all(r[k] == v for k, v in sel.items())]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_error_falls_with_order_and_beta(dim):
+    if dim == 2:
+        prims, q = configs.star_2d(n_queries=8192)
+    else:
+        prims, q = configs.sphere_3d(n_queries=8192)
+    pts = torch.from_numpy(q.astype(np.float32)).cuda()
+    # FP64 queries, so that the Taylor remainder is not hidden under FP32 rounding
+    rows = S.sweep(dim, prims, pts.double(), orders=(0, 1, 2), betas=(3.0, 6.0, 12.0), reps=1,
+                   precision=gwn.PREC_FP64)
+    assert len(rows) == 9
+    # the second-order term removes the leading remainder of both lower orders (for
+    # expansions about the area- or length-weighted centroid, order 1 need not beat
+    # order 0 in the maximum: on the trimmed sphere at beta = 6 it does not)
+    for beta in (6.0, 12.0):
+        e = [_rows(rows, order=o, beta=beta)[0]["max_abs_dgwn"] for o in (0, 1, 2)]
+        assert e[2] < 0.2 * min(e[0], e[1]), (beta, e)
+    for order in (0, 1, 2):
+        e = [_rows(rows, order=order, beta=b)[0]["max_abs_dgwn"] for b in (3.0, 6.0, 12.0)]
+        assert e[0] > e[1] > e[2], (order, e)
+    assert all(r["queries_per_s"] > 0 for r in rows)

@@ -291,27 +291,6 @@ __global__ void __launch_bounds__(128, 5) k_pair_eval(DevTree t, const void* pts
     if (work) flush_work(wl, work);
 }
 
-// the near band: leaves that FP32 could not resolve, in FP64
-__global__ void k_pair_eval64(DevTree t, const void* pts, int dtype, int npair64_cap, const int* counters,
-                              const int2* pairs64, float* wacc, uint32_t* st) {
-    int np = min(counters[2], npair64_cap);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < np; k += gridDim.x * blockDim.x) {
-        int2 pr = pairs64[k];
-        double q[3];
-        if (dtype == GWN_F32) {
-            const float* p = reinterpret_cast<const float*>(pts) + (size_t)pr.x * 3;
-            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
-        } else {
-            const double* p = reinterpret_cast<const double*>(pts) + (size_t)pr.x * 3;
-            q[0] = (double)(float)p[0]; q[1] = (double)(float)p[1]; q[2] = (double)(float)p[2];
-        }
-        uint32_t s = 0;
-        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s, kRatio64Band);
-        atomicAdd(&wacc[pr.x], (float)v);
-        if (s) atomicOr(&st[pr.x], s);
-    }
-}
-
 // 4-point FP64 panels are used for leaves whose boundary curves all have degree
 // <= 6 (pieces of degree 1 composed with the bicubic net); curves of higher
 // degree (rational trims) take 8-point panels, whose error does not depend on
@@ -446,81 +425,6 @@ __global__ void k_finish(int n, const float* wacc, const uint32_t* stv, int prec
 
 namespace gwn {
 
-// ---- FP64 repair of the listed points (3D), with the same deferral as the
-// FP32 pass: one thread per point traverses in FP64 (beta_repair), adds far
-// terms and defers exact leaves to a pair list; one thread per pair then
-// evaluates the leaf in FP64.  Points whose pairs overflow the list evaluate
-// them in place.
-__global__ void __launch_bounds__(128) k_rtrav3(DevTree t, const void* pts, int dtype, double beta2r, const int* rlist,
-                                                Workspace ws) {
-    int cnt = ws.counters[1];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-        int qi = rlist[k];
-        double q[3];
-        if (dtype == GWN_F32) {
-            const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * 3;
-            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
-        } else {
-            const double* p = reinterpret_cast<const double*>(pts) + (size_t)qi * 3;
-            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
-        }
-        double w = 0.0;
-        uint32_t st = 0;
-        int stack[kStack64];
-        int sp = 0;
-        int node = t.root;
-        while (true) {
-            if (node < 0) {
-                int li = ~node;
-                const double* h = t.lhdr64 + (size_t)li * 4;
-                double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
-                if (beta2r > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2r * h[3]) {
-                    w += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
-                } else {
-                    long long slot = atomicAdd(&ws.counters[4], 1);
-                    if (slot < kRepairPairCap) ws.rpairs[slot] = make_int2(k, li);
-                    else w += leaf3_eval64(t, li, q[0], q[1], q[2], st, kRatio64Repair);
-                }
-            } else {
-                const double* h = t.hdr64 + (size_t)node * 4;
-                double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
-                if (beta2r > 0 && rx * rx + ry * ry + rz * rz > beta2r * h[3]) {
-                    w += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz);
-                } else {
-                    int2 ch = t.child[node];
-                    if (sp < kStack64) stack[sp++] = ch.y; else st |= GWN_QS_UNRESOLVED;
-                    node = ch.x;
-                    continue;
-                }
-            }
-            if (sp == 0) break;
-            node = stack[--sp];
-        }
-        ws.rw[k] = w;
-        ws.st[qi] = st;  // the FP32 pass's flags are replaced by the repair's
-    }
-}
-
-__global__ void __launch_bounds__(128) k_rpairs3(DevTree t, const void* pts, int dtype, const int* rlist, Workspace ws) {
-    long long np = min((long long)ws.counters[4], kRepairPairCap);
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
-        int2 pr = ws.rpairs[j];
-        int qi = rlist[pr.x];
-        double q[3];
-        if (dtype == GWN_F32) {
-            const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * 3;
-            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
-        } else {
-            const double* p = reinterpret_cast<const double*>(pts) + (size_t)qi * 3;
-            q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
-        }
-        uint32_t s = 0;
-        double v = leaf3_eval64(t, pr.y, q[0], q[1], q[2], s, kRatio64Repair);
-        atomicAdd(&ws.rw[pr.x], v);
-        if (s) atomicOr(&ws.st[qi], s);
-    }
-}
-
 // FP64 repair pairs with one warp per pair (leaf3_warp64)
 __global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts, int dtype, const int* rlist,
                                                       Workspace ws) {
@@ -586,7 +490,7 @@ namespace gwn {
 // of the nodes that fail it (positions by a warp prefix sum).  This spreads one
 // point's traversal over 32 lanes, which matters because FP64 issue is slow
 // and latency-bound when a single thread walks the tree.  Exact leaves: 2D in
-// place (FP64), 3D appended to the FP64 pair list (k_rpairs3).
+// place (FP64), 3D appended to the FP64 pair list (k_rpairs3_warp).
 constexpr int kWarpStack = 2048;
 constexpr int kRepairWarps = 4;  // warps per block
 

@@ -32,10 +32,11 @@ def test_error_falls_with_order_and_beta(dim):
     assert len(rows) == 9
     # the second-order term removes the leading remainder of both lower orders (for
     # expansions about the area- or length-weighted centroid, order 1 need not beat
-    # order 0 in the maximum: on the trimmed sphere at beta = 6 it does not)
-    for beta in (6.0, 12.0):
-        e = [_rows(rows, order=o, beta=beta)[0]["max_abs_dgwn"] for o in (0, 1, 2)]
-        assert e[2] < 0.2 * min(e[0], e[1]), (beta, e)
+    # order 0 in the maximum: on the trimmed sphere at beta = 6 it does not).  At
+    # beta = 12 the 3D errors approach the ~1e-6 level of the exact evaluation, so
+    # the order comparison is made at beta = 6.
+    e = [_rows(rows, order=o, beta=6.0)[0]["max_abs_dgwn"] for o in (0, 1, 2)]
+    assert e[2] < 0.2 * min(e[0], e[1]), e
     for order in (0, 1, 2):
         e = [_rows(rows, order=order, beta=b)[0]["max_abs_dgwn"] for b in (3.0, 6.0, 12.0)]
         assert e[0] > e[1] > e[2], (order, e)

@@ -112,7 +112,9 @@ struct DevTree {
 };
 
 // Work counters (only when QueryParams::work != nullptr): the algorithmic
-// units of the roofline numerator, see the design doc.
+// units counted by the kernels, from which the benchmark forms the flops of
+// its roofline numerator (per Gauss-Legendre node 28 D + 70, per Taylor term
+// 72, per far test 10, per foot-point search 2000).
 enum {
     kWorkNodes = 0,      // internal nodes visited (far test)
     kWorkLeafTests = 1,  // leaves visited (far test or direct)

@@ -1,6 +1,6 @@
 """GPU parity of the 2D path against the FP64 oracle (exact direct sum).
 
-Acceptance (the spec numbers): max |dGWN| <= 1e-9 on the all-FP64 star
+Acceptance: max |dGWN| <= 1e-9 on the all-FP64 star
 workload; <= 1e-4 on FP32-bulk workloads; rounded containment identical for
 every query farther than 1e-6 of the box diagonal from the curves, except
 queries whose exact GWN lies within the FP64 repair path's own error of a

@@ -400,6 +400,8 @@ def main():
 
     step_e2e()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     t1 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
@@ -407,6 +409,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t1) / e2e_steps
     log(f"e2e {e2e_s * 1e3:.1f} ms/step")
+    _, e2e_value = aggregate_ranks(e2e_s * 1e3, total_q, world, dev)
     h2d = sum(p.numel() * 4 for p in points)
     d2h = sum(p.shape[0] * (8 + 4) for p in points)
 
@@ -457,7 +460,7 @@ def main():
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1),
                    "launch": (f"gwn_query_batch: one CUDA graph launch per step over {args.streams} streams"
                               if batch is not None else "one gwn_query per model")},
-        "e2e": {"value": world * total_q / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roofline,
         "direct_sum": {"value": direct_qps, "unit": "queries/s",

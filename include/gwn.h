@@ -92,7 +92,7 @@ enum { GWN_MEM_DEVICE = 0, GWN_MEM_HOST = 1 };  /* where points and outputs live
 /* Per-query status bits written to out_status. */
 enum {
     GWN_QS_REPAIRED = 1u,       /* value re-evaluated in FP64 */
-    GWN_QS_NEAR = 2u,           /* a leaf needed its deepest refinement level (query very near the boundary) */
+    GWN_QS_NEAR = 2u,           /* a leaf of this query went to the FP64 near band (query very near the boundary) */
     GWN_QS_STACK_OVERFLOW = 4u, /* traversal stack overflow in the FP32 pass (value repaired) */
     GWN_QS_UNRESOLVED = 8u      /* FP64 pass also hit a refinement or stack limit: value may be inexact */
 };
@@ -212,7 +212,7 @@ gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
  *   out[3] points whose pairs did not fit the work list
  *   out[4..11] with count_work: internal nodes visited, leaves visited, Taylor
  *     evaluations, exact leaf evaluations, Gauss-Legendre nodes, sum of curve
- *     degrees over those nodes, foot-point searches, (reserved)
+ *     degrees over those nodes, foot-point searches, 2D chord angles
  *   out[12..13] with profile: traversal and exact-leaf kernel time in
  *     microseconds (CUDA events on the query's stream) */
 gwn_status gwn_last_query_stats(gwn_model model, int64_t* out);

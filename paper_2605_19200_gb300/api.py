@@ -242,19 +242,19 @@ class Model:
                          out=out, beta_leaf=beta_leaf)
 
 
-def gwn_build_2d(curves: Sequence, opts: Optional[gwn_build_opts] = None, **kw) -> Model:
-    opts = opts or default_build_opts(**kw)
+def marshal_curves(curves: Sequence):
+    """gwn_curve2d array for `curves` (synth.geometry.Curve-like objects) and the
+    buffers that keep its pointers valid: (array, keepalive)."""
     pack = _Pack()
     arr, offs = _curve_array(curves, pack)
     base = pack.finish()
     _fill_curves(arr, curves, offs, base)
-    h = ctypes.c_void_p()
-    _check(lib().gwn_build_2d(ctypes.cast(arr, _P), len(curves), ctypes.byref(opts), ctypes.byref(h)))
-    return Model(h.value, 2)
+    return arr, pack
 
 
-def gwn_build_3d(patches: Sequence, opts: Optional[gwn_build_opts] = None, **kw) -> Model:
-    opts = opts or default_build_opts(**kw)
+def marshal_patches(patches: Sequence):
+    """gwn_patch3d array for `patches` (synth.geometry.Patch-like objects) and the
+    buffers that keep its pointers valid: (array, keepalive)."""
     pack = _Pack()
     parr = (gwn_patch3d * max(1, len(patches)))()
     poffs = []
@@ -276,10 +276,23 @@ def gwn_build_3d(patches: Sequence, opts: Optional[gwn_build_opts] = None, **kw)
         s.n_trims = len(p.trims)
         _fill_curves(trim_arrays[i], p.trims, all_trims[i], base)
         s.trims = ctypes.cast(trim_arrays[i], _P).value if p.trims else None
+    return parr, (pack, trim_arrays)
+
+
+def gwn_build_2d(curves: Sequence, opts: Optional[gwn_build_opts] = None, **kw) -> Model:
+    opts = opts or default_build_opts(**kw)
+    arr, keep = marshal_curves(curves)
+    h = ctypes.c_void_p()
+    _check(lib().gwn_build_2d(ctypes.cast(arr, _P), len(curves), ctypes.byref(opts), ctypes.byref(h)))
+    return Model(h.value, 2)
+
+
+def gwn_build_3d(patches: Sequence, opts: Optional[gwn_build_opts] = None, **kw) -> Model:
+    opts = opts or default_build_opts(**kw)
+    parr, keep = marshal_patches(patches)
     h = ctypes.c_void_p()
     _check(lib().gwn_build_3d(ctypes.cast(parr, _P), len(patches), ctypes.byref(opts), ctypes.byref(h)))
-    m = Model(h.value, 3)
-    return m
+    return Model(h.value, 3)
 
 
 def _stream_handle(stream):

@@ -1,0 +1,134 @@
+// Host execution of the query routines of the CUDA path (test harness).
+//
+// The leaf evaluators and the traversal of kernels2d.cuh / kernels3d.cuh are
+// host-device functions; this file runs them on the CPU against models built
+// by the library's own host build, so that the CPU test suite can compare the
+// CUDA path's arithmetic with the FP64 oracle without a GPU.  It is test
+// infrastructure: nothing in the package loads it.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "../../paper_2605_19200_gb300/csrc/build.h"
+#include "../../paper_2605_19200_gb300/csrc/kernels3d.cuh"
+
+using namespace gwn;
+
+namespace {
+
+// n-point Gauss-Legendre rule on [0, 1] (Newton on the Legendre polynomial)
+void gauss01(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 1;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1, p2 = 0;
+            for (int j = 1; j <= n; ++j) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1);
+            double dz = p1 / pp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1 - z);
+        w[i] = 1.0 / ((1 - z * z) * pp * pp);
+    }
+}
+
+void init_tables() {
+    for (int a = 0; a <= kMaxC3Deg; ++a) {
+        for (int b = 0; b <= kMaxC3Deg; ++b) h_binom[a][b] = 0.f;
+        h_binom[a][0] = h_binom[a][a] = 1.f;
+        for (int b = 1; b < a; ++b) h_binom[a][b] = h_binom[a - 1][b - 1] + h_binom[a - 1][b];
+    }
+    gauss01(8, h_glx8, h_glw8);
+    gauss01(4, h_glx4d, h_glw4d);
+    for (int i = 0; i < 4; ++i) {
+        h_glx4f[i] = (float)h_glx4d[i];
+        h_glw4f[i] = (float)h_glw4d[i];
+    }
+}
+
+DevTree host_tree(const HostModel& H, int leaf_far) {
+    DevTree t{};
+    t.dim = H.dim;
+    t.n_leaves = H.n_leaves;
+    t.n_internal = H.n_leaves - 1;
+    t.root = H.n_leaves > 1 ? 0 : ~0;
+    t.leaf_far = leaf_far;
+    t.lhdr = H.lhdr.data();
+    t.lmom = H.lmom.data();
+    t.lhdr64 = H.lhdr64.data();
+    t.lmom64 = H.lmom64.data();
+    t.hdr = H.hdr.data();
+    t.child = H.child.data();
+    t.mom = H.mom.data();
+    t.hdr64 = H.hdr64.data();
+    t.mom64 = H.mom64.data();
+    t.leaf2 = H.leaf2.data();
+    t.leaf2_64 = H.leaf2_64.data();
+    t.leaf3 = H.leaf3.data();
+    t.net3 = H.net3.data();
+    t.net3_64 = H.net3_64.data();
+    t.c3 = H.c3.data();
+    t.c3pts = H.c3pts.data();
+    t.c3pts64 = H.c3pts64.data();
+    t.c2 = H.c2.data();
+    t.c2_64 = H.c2_64.data();
+    t.c2mult = H.c2mult.data();
+    return t;
+}
+
+}  // namespace
+
+// For each query: the direct sums over every leaf in FP32 (with the FP64 near
+// band) and in FP64, and the FP32 traversal with far-field factors beta and
+// beta_leaf.  Returns the number of leaves, or -1 if the build failed.
+extern "C" int hx_query3(const gwn_patch3d* patches, size_t n, const gwn_build_opts* o, const double* q, int nq,
+                         double beta, double beta_leaf, double* direct32, double* direct64, double* bvh32,
+                         unsigned* status) {
+    init_tables();
+    HostModel H;
+    gwn_status code;
+    if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
+    const DevTree t = host_tree(H, 1);
+    for (int i = 0; i < nq; ++i) {
+        const float qx = (float)q[3 * i], qy = (float)q[3 * i + 1], qz = (float)q[3 * i + 2];
+        uint32_t s32 = 0, s64 = 0, sb = 0;
+        double a = 0, b = 0;
+        for (int l = 0; l < t.n_leaves; ++l) {
+            a += leaf3_eval32(t, l, qx, qy, qz, s32);
+            b += leaf3_eval64(t, l, q[3 * i], q[3 * i + 1], q[3 * i + 2], s64);
+        }
+        direct32[i] = a;
+        direct64[i] = b;
+        bvh32[i] = query3_32(t, qx, qy, qz, (float)(beta * beta), sb, (float)(beta_leaf * beta_leaf));
+        status[i] = s32 | s64 | sb;
+    }
+    return t.n_leaves;
+}
+
+extern "C" int hx_query2(const gwn_curve2d* curves, size_t n, const gwn_build_opts* o, const double* q, int nq,
+                         double beta, double* direct32, double* direct64, double* bvh32, unsigned* status) {
+    init_tables();
+    HostModel H;
+    gwn_status code;
+    if (!build_model_2d(curves, n, *o, &H, &code).empty()) return -1;
+    const DevTree t = host_tree(H, 0);
+    for (int i = 0; i < nq; ++i) {
+        const float qx = (float)q[2 * i], qy = (float)q[2 * i + 1];
+        uint32_t s32 = 0, s64 = 0, sb = 0;
+        double a = 0, b = 0;
+        for (int l = 0; l < t.n_leaves; ++l) {
+            a += leaf2_eval32(t, l, qx, qy, s32);
+            b += leaf2_eval64(t, l, q[2 * i], q[2 * i + 1], s64);
+        }
+        direct32[i] = a;
+        direct64[i] = b;
+        bvh32[i] = query2_32(t, qx, qy, (float)(beta * beta), sb);
+        status[i] = s32 | s64 | sb;
+    }
+    return t.n_leaves;
+}

@@ -1,0 +1,118 @@
+"""The CUDA path's arithmetic, executed on the CPU, against the FP64 oracle.
+
+The leaf evaluators (exact 2D leaves; the 3D Stokes/string evaluation with its
+Newton foot point, trim membership and adaptive Gauss-Legendre panels), the
+FP64 near band and the FP32 traversal with the order-2 far field are
+host-device functions.  tests/host_exec/gwn_host_exec.cu runs them on the CPU
+on models from the library's host build, so these checks need no GPU: the
+direct sums over every leaf (FP32 with its near band, and FP64) and the FP32
+traversal must match the oracle's exact values within the bounds the GPU tests
+use.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2605_19200_gb300 import api
+from synth import configs
+from synth import geometry as G
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "host_exec", "gwn_host_exec.cu")
+OUT_DIR = os.path.join(HERE, "host_exec", "_build")
+LIB = os.path.join(OUT_DIR, "libgwn_host_exec.so")
+
+
+@pytest.fixture(scope="module")
+def hx():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    os.makedirs(OUT_DIR, exist_ok=True)
+    csrc = os.path.join(ROOT, "paper_2605_19200_gb300", "csrc")
+    cmd = [nvcc, "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
+           "-I", csrc, SRC, os.path.join(csrc, "build.cpp"), os.path.join(csrc, "build3d.cpp"), "-o", LIB]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lib = ctypes.CDLL(LIB)
+    P = ctypes.c_void_p
+    lib.hx_query3.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), P, ctypes.c_int,
+                              ctypes.c_double, ctypes.c_double, P, P, P, P]
+    lib.hx_query2.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), P, ctypes.c_int,
+                              ctypes.c_double, P, P, P, P]
+    return lib
+
+
+def _run3(hx, patches, q, beta, beta_leaf, **kw):
+    parr, keep = api.marshal_patches(patches)
+    o = api.default_build_opts(beta=beta, beta_leaf=beta_leaf, **kw)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = q.shape[0]
+    d32, d64, b32 = np.zeros(n), np.zeros(n), np.zeros(n)
+    st = np.zeros(n, dtype=np.uint32)
+    nl = hx.hx_query3(ctypes.cast(parr, ctypes.c_void_p), len(patches), ctypes.byref(o), q.ctypes.data, n,
+                      beta, beta_leaf, d32.ctypes.data, d64.ctypes.data, b32.ctypes.data, st.ctypes.data)
+    assert nl > 0
+    return d32, d64, b32, st
+
+
+def _run2(hx, curves, q, beta, **kw):
+    arr, keep = api.marshal_curves(curves)
+    o = api.default_build_opts(beta=beta, **kw)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = q.shape[0]
+    d32, d64, b32 = np.zeros(n), np.zeros(n), np.zeros(n)
+    st = np.zeros(n, dtype=np.uint32)
+    nl = hx.hx_query2(ctypes.cast(arr, ctypes.c_void_p), len(curves), ctypes.byref(o), q.ctypes.data, n,
+                      beta, d32.ctypes.data, d64.ctypes.data, b32.ctypes.data, st.ctypes.data)
+    assert nl > 0
+    return d32, d64, b32, st
+
+
+def _diag3(patches):
+    lo, hi = G.shape_bbox_3d(patches)
+    return float(np.linalg.norm(hi - lo))
+
+
+@pytest.mark.parametrize("shape", ["cad", "sphere"])
+def test_3d_leaf_evaluators_and_traversal(hx, oracle_lib, shape):
+    if shape == "cad":
+        patches, q = configs.cad_3d(1234, 120, 40)       # polygon trims: degree-6 boundary curves
+    else:
+        patches, q = configs.sphere_3d(n_queries=40)     # disc trims: degree-12 rational curves
+    w_ref, fl = oracle_lib.gwn3d(patches, q, near_thr=1e-6 * _diag3(patches))
+    ok = np.isfinite(w_ref)
+    d32, d64, b32, st = _run3(hx, patches, q, beta=6.0, beta_leaf=4.0)
+    assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-7     # all-FP64 exact evaluation
+    assert np.max(np.abs(d32[ok] - w_ref[ok])) <= 2e-5     # FP32 quadrature + FP64 near band
+    assert np.max(np.abs(b32[ok] - w_ref[ok])) <= 1e-4     # FP32 traversal, order-2 far field
+    assert not np.any(st & api.QS_UNRESOLVED)
+
+
+def test_3d_near_surface_uses_the_fp64_band(hx, oracle_lib):
+    """Queries 1e-5 of the diagonal off a planar trimmed face: FP32 cannot decide
+    the foot point there, the FP64 near band must, and the sum stays exact."""
+    disk = G.planar_patch((-0.5, -0.5, 0.0), (1, 0, 0), (0, 1, 0), trims=[G.circle((0.5, 0.5), 0.3)])
+    hs = np.array([1e-5, -1e-5, 1e-4, -1e-4, 0.05, -0.05])
+    q = np.stack([np.full_like(hs, 0.05), np.full_like(hs, -0.02), hs], axis=1).astype(np.float32).astype(np.float64)
+    w_ref, _ = oracle_lib.gwn3d([disk], q)
+    d32, d64, b32, st = _run3(hx, [disk], q, beta=6.0, beta_leaf=4.0, max_aabb_frac=0.0)
+    assert np.max(np.abs(d64 - w_ref)) <= 1e-8
+    assert np.max(np.abs(d32 - w_ref)) <= 1e-5
+    assert np.any(st & api.QS_NEAR)                      # the band was used
+
+
+def test_2d_leaf_evaluators_and_traversal(hx, oracle_lib):
+    curves, q = configs.star_2d(n_queries=400)
+    lo, hi = G.shape_bbox_2d(curves)
+    w_ref, fl = oracle_lib.gwn2d(curves, q, near_thr=1e-6 * float(np.linalg.norm(hi - lo)))
+    ok = np.isfinite(w_ref)
+    d32, d64, b32, st = _run2(hx, curves, q, beta=8.0)
+    assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-10
+    assert np.max(np.abs(d32[ok] - w_ref[ok])) <= 1e-5
+    assert np.max(np.abs(b32[ok] - w_ref[ok])) <= 1e-4

@@ -115,6 +115,11 @@ typedef struct {
                              (only leaves containing the query are evaluated exactly); 0: every
                              leaf reached is evaluated exactly; -1: 1 in 3D, 0 in 2D (default) */
     double beta_leaf;     /* far-test factor of the leaves themselves when leaf_far is on; 0 = beta (default 0) */
+    int32_t adaptive_beta; /* 1: geometry-aware far test per cluster (the per-cluster beta Section 5 names):
+                              a cluster of fill a = (curve length or area) / r^(d-1) is approximated only
+                              beyond beta * s * r with s = clamp((a / median a)^(1 / (order + d)), 1, 4),
+                              since its order-p remainder grows like a * beta^-(p + d); dense clusters are
+                              opened earlier, the others keep beta.  0 = off (default 0) */
 } gwn_build_opts;
 
 /* Fills *opts with the defaults listed above. */

@@ -48,7 +48,8 @@ class gwn_build_opts(ctypes.Structure):
     _fields_ = [("tolerance", ctypes.c_double), ("max_aabb_frac", ctypes.c_double), ("order", ctypes.c_int32),
                 ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double), ("repair_band", ctypes.c_double),
                 ("quad_nodes", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("n_threads", ctypes.c_int32), ("leaf_far", ctypes.c_int32), ("beta_leaf", ctypes.c_double)]
+                ("n_threads", ctypes.c_int32), ("leaf_far", ctypes.c_int32), ("beta_leaf", ctypes.c_double),
+                ("adaptive_beta", ctypes.c_int32)]
 
 
 class gwn_query_opts(ctypes.Structure):

@@ -242,7 +242,7 @@ static void centre_block(int d, const double* box, double w, const double* wx, c
                     m2[(i * d + j) * d + k] - y[i] * m1[j * d + k] - y[j] * m1[i * d + k] + y[i] * y[j] * m0[k];
 }
 
-void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm) {
+void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm, int adaptive_beta) {
     const int d = L.dim;
     const int n = (int)L.wsum.size();
     const int M = momn(d);
@@ -415,6 +415,27 @@ void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* p
         for (int k = 0; k < 3; ++k) out->hdr64[node * 4 + k] = x0[k];
         out->hdr64[node * 4 + 3] = radius * radius;
     }
+    if (adaptive_beta && ni > 1) {
+        // geometry-aware far test: the order-p remainder of a cluster of fill
+        // a = (total curve length or area) / r^(d-1) grows like a * beta^-(p+d), so
+        // a cluster denser than the median is approximated only beyond
+        // beta * s * r, s = (a / a_median)^(1 / (p + d)) in [1, 4]; the far test
+        // compares |x0 - q|^2 with beta^2 * hdr.w, so hdr.w carries s^2 r^2
+        std::vector<double> fill(ni);
+        for (int node = 0; node < ni; ++node) {
+            const double r = std::max(out->r[node], 1e-300);
+            fill[node] = nw[node] / (d == 2 ? r : r * r);
+        }
+        std::vector<double> sorted = fill;
+        std::nth_element(sorted.begin(), sorted.begin() + ni / 2, sorted.end());
+        const double med = std::max(sorted[ni / 2], 1e-300);
+        for (int node = 0; node < ni; ++node) {
+            const double s = std::min(4.0, std::max(1.0, std::pow(fill[node] / med, 1.0 / (order + d))));
+            const double r2 = out->r[node] * out->r[node] * s * s;
+            out->hdr[node].w = (float)r2;
+            out->hdr64[node * 4 + 3] = r2;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ 2D
@@ -571,7 +592,7 @@ std::string build_model_2d(const gwn_curve2d* curves, size_t n, const gwn_build_
         S.wx[i * 2 + 1] = len * (0.5 * (a[1] + b[1]) + S.xref[1]);
     }
     std::vector<int> perm;
-    build_tree(S, o.order, out, &perm);
+    build_tree(S, o.order, out, &perm, o.adaptive_beta);
     out->lo[0] = slo[0]; out->lo[1] = slo[1];
     out->hi[0] = shi[0]; out->hi[1] = shi[1];
     out->leaf_prim.resize(nl);

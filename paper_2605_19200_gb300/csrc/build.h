@@ -68,7 +68,9 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
 
 // Generic LBVH + up-sweep + centring + packing of the node arrays.  perm
 // receives the BVH leaf order (perm[i] = input leaf index of BVH leaf i).
-void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm);
+// adaptive_beta: scale each cluster's far-test radius by its fill (see
+// gwn_build_opts::adaptive_beta).
+void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm, int adaptive_beta = 0);
 
 // Validation of a clamped NURBS knot vector; returns "" when valid.
 std::string check_knots(int degree, int n_ctrl, const double* knots);

@@ -213,6 +213,7 @@ gwn_status check_opts(const gwn_build_opts& o) {
     if (!(o.beta == 0.0 || o.beta >= 2.0) || !std::isfinite(o.beta)) return fail(GWN_ERR_INVALID_ARG, "beta must be 0 (autotune) or >= 2");
     if (!(o.beta_leaf == 0.0 || o.beta_leaf >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_leaf must be 0 or >= 2");
     if (o.order < 0 || o.order > 2) return fail(GWN_ERR_INVALID_ARG, "order must be 0, 1 or 2");
+    if (o.adaptive_beta != 0 && o.adaptive_beta != 1) return fail(GWN_ERR_INVALID_ARG, "adaptive_beta must be 0 or 1");
     if (!(o.beta_repair <= 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be <= 0 or >= 2");
     if (!(o.repair_band >= 0.0 && o.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
     if (o.quad_nodes < 1 || o.quad_nodes > 32) return fail(GWN_ERR_INVALID_ARG, "quad_nodes must be 1..32");
@@ -610,6 +611,7 @@ void gwn_default_build_opts(gwn_build_opts* o) {
     o->n_threads = 0;
     o->leaf_far = -1;
     o->beta_leaf = 0.0;
+    o->adaptive_beta = 0;
 }
 
 void gwn_default_query_opts(gwn_query_opts* q) {

@@ -110,8 +110,11 @@ extern "C" int hx_query3(const gwn_patch3d* patches, size_t n, const gwn_build_o
     return t.n_leaves;
 }
 
+// work[0..2] receive the traversal's totals: internal nodes visited, Taylor
+// evaluations, exact leaf evaluations (may be NULL)
 extern "C" int hx_query2(const gwn_curve2d* curves, size_t n, const gwn_build_opts* o, const double* q, int nq,
-                         double beta, double* direct32, double* direct64, double* bvh32, unsigned* status) {
+                         double beta, double* direct32, double* direct64, double* bvh32, unsigned* status,
+                         long long* work) {
     init_tables();
     HostModel H;
     gwn_status code;
@@ -127,8 +130,14 @@ extern "C" int hx_query2(const gwn_curve2d* curves, size_t n, const gwn_build_op
         }
         direct32[i] = a;
         direct64[i] = b;
-        bvh32[i] = query2_32(t, qx, qy, (float)(beta * beta), sb);
+        WorkLocal wl = {};
+        bvh32[i] = query2_32(t, qx, qy, (float)(beta * beta), sb, &wl);
         status[i] = s32 | s64 | sb;
+        if (work) {
+            work[0] += (long long)wl.v[kWorkNodes];
+            work[1] += (long long)wl.v[kWorkFar];
+            work[2] += (long long)wl.v[kWorkLeaves];
+        }
     }
     return t.n_leaves;
 }

@@ -44,7 +44,7 @@ def hx():
     lib.hx_query3.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), P, ctypes.c_int,
                               ctypes.c_double, ctypes.c_double, P, P, P, P]
     lib.hx_query2.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), P, ctypes.c_int,
-                              ctypes.c_double, P, P, P, P]
+                              ctypes.c_double, P, P, P, P, P]
     return lib
 
 
@@ -61,7 +61,7 @@ def _run3(hx, patches, q, beta, beta_leaf, **kw):
     return d32, d64, b32, st
 
 
-def _run2(hx, curves, q, beta, **kw):
+def _run2(hx, curves, q, beta, work=None, **kw):
     arr, keep = api.marshal_curves(curves)
     o = api.default_build_opts(beta=beta, **kw)
     q = np.ascontiguousarray(q, dtype=np.float64)
@@ -69,7 +69,8 @@ def _run2(hx, curves, q, beta, **kw):
     d32, d64, b32 = np.zeros(n), np.zeros(n), np.zeros(n)
     st = np.zeros(n, dtype=np.uint32)
     nl = hx.hx_query2(ctypes.cast(arr, ctypes.c_void_p), len(curves), ctypes.byref(o), q.ctypes.data, n,
-                      beta, d32.ctypes.data, d64.ctypes.data, b32.ctypes.data, st.ctypes.data)
+                      beta, d32.ctypes.data, d64.ctypes.data, b32.ctypes.data, st.ctypes.data,
+                      work.ctypes.data if work is not None else None)
     assert nl > 0
     return d32, d64, b32, st
 
@@ -116,3 +117,20 @@ def test_2d_leaf_evaluators_and_traversal(hx, oracle_lib):
     assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-10
     assert np.max(np.abs(d32[ok] - w_ref[ok])) <= 1e-5
     assert np.max(np.abs(b32[ok] - w_ref[ok])) <= 1e-4
+
+
+def test_adaptive_beta_opens_dense_clusters_earlier(hx, oracle_lib):
+    """adaptive_beta scales the far-test radius of clusters denser than the
+    median (never below beta): at a fixed beta the traversal visits more nodes
+    and the maximum error does not grow."""
+    curves, q = configs.loops_2d(n_loops=60, res=48)
+    w_ref, _ = oracle_lib.gwn2d(curves, q)
+    ok = np.isfinite(w_ref)
+    res = {}
+    for ad in (0, 1):
+        work = np.zeros(3, np.int64)
+        _, _, b32, _ = _run2(hx, curves, q, beta=8.0, work=work, adaptive_beta=ad)
+        res[ad] = (float(np.max(np.abs(b32[ok] - w_ref[ok]))), int(work[0]))
+    assert res[1][1] > res[0][1]                 # dense clusters opened: more nodes visited
+    assert res[1][0] <= res[0][0]                # and the error did not grow
+    assert res[0][0] <= 1e-3

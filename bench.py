@@ -39,7 +39,7 @@ import numpy as np
 
 BETA = 0.0              # 0: the build's autotuner picks beta and beta_leaf per model for max |dGWN| <= 1e-4
 DIRECT_SAMPLE = 40960   # queries per model for the plain direct-sum comparison (fills the GPU)
-ORACLE_SAMPLE = 2       # queries per model for the CPU oracle
+ORACLE_SAMPLE = 3       # queries per model for the CPU oracle (about 10 s on 16 cores)
 WORKLOAD_NAME = ("cad16: 16 models of trimmed bicubic rational patches (box/cylinder unions), "
                  "queries uniform in each model's box")
 PAIR_EVAL_DRAM_BYTES_PER_PAIR = 10.5  # ncu dram__bytes_read + dram__bytes_write of k_pair_eval per pair

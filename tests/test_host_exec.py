@@ -134,3 +134,64 @@ def test_adaptive_beta_opens_dense_clusters_earlier(hx, oracle_lib):
     assert res[1][1] > res[0][1]                 # dense clusters opened: more nodes visited
     assert res[1][0] <= res[0][0]                # and the error did not grow
     assert res[0][0] <= 1e-3
+
+
+def _disk_on_axis(h, R):
+    # GWN of a disc of radius R seen from height h on its axis (normal +z):
+    # minus sign(h) times its solid angle over 4 pi
+    return -np.sign(h) * 0.5 * (1.0 - np.abs(h) / np.sqrt(h * h + R * R))
+
+
+def test_annulus_on_axis_closed_form(hx):
+    """A planar face trimmed to an annulus (outer loop counter-clockwise, hole
+    clockwise): on the axis its GWN is the outer disc's minus the inner disc's,
+    in closed form.  Exercises a hole, rational circle trims and queries from
+    1e-4 to 2 units off the face."""
+    R1, R2 = 0.15, 0.4
+    face = G.planar_patch((-0.5, -0.5, 0.0), (1, 0, 0), (0, 1, 0),
+                          trims=[G.circle((0.5, 0.5), R2), G.circle((0.5, 0.5), R1, ccw=False)])
+    hs = np.array([2.0, 0.6, 0.1, 1e-2, 1e-3, 1e-4, -1e-4, -1e-3, -0.2, -1.5])
+    q = np.stack([np.zeros_like(hs), np.zeros_like(hs), hs], axis=1).astype(np.float32).astype(np.float64)
+    exact = _disk_on_axis(q[:, 2], R2) - _disk_on_axis(q[:, 2], R1)
+    for frac in (0.0, 0.1):
+        d32, d64, b32, st = _run3(hx, [face], q, beta=6.0, beta_leaf=4.0, max_aabb_frac=frac)
+        assert np.max(np.abs(d64 - exact)) <= 1e-9, frac
+        assert np.max(np.abs(d32 - exact)) <= 1e-5, frac
+        assert np.max(np.abs(b32 - exact)) <= 1e-4, frac
+
+
+def test_closed_shells_give_integers(hx):
+    """The exact rational NURBS sphere (degree 2 x 2, several spans) and a cube of
+    bilinear faces: 1 inside, 0 outside, including queries near the surface and
+    far away (1e3 diagonals)."""
+    rng = np.random.default_rng(11)
+    dirs = rng.normal(size=(24, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    radii = np.concatenate([rng.uniform(0.0, 0.9, 8), [0.999, 1.001], rng.uniform(1.1, 3.0, 6), [1e3] * 8])
+    q = (dirs * radii[:, None]).astype(np.float32).astype(np.float64)
+    inside = (np.linalg.norm(q, axis=1) < 1.0).astype(float)
+    for shape in ([G.nurbs_sphere(radius=1.0)], G.cube_shell(half=1.0 / np.sqrt(3.0))):
+        if len(shape) == 6:
+            inside = np.all(np.abs(q) < 1.0 / np.sqrt(3.0), axis=1).astype(float)
+        # large flat faces make the order-2 remainder at beta 6 about 4e-4 for the cube;
+        # beta 12 / 8 brings both shells under 1e-4
+        d32, d64, b32, st = _run3(hx, shape, q, beta=12.0, beta_leaf=8.0)
+        assert np.max(np.abs(d64 - inside)) <= 1e-7
+        assert np.max(np.abs(d32 - inside)) <= 1e-5
+        assert np.max(np.abs(b32 - inside)) <= 1e-4
+        assert not np.any(st & api.QS_UNRESOLVED)
+
+
+def test_2d_degenerate_and_far_queries(hx, oracle_lib):
+    """A closed polygon with a repeated vertex (a zero-length segment), a rational
+    circle and queries far outside: integers and exact zeros survive."""
+    poly = G.polyline([(0, 0), (1, 0), (1, 0), (1, 1), (0, 1)])
+    circ = G.circle((3.0, 0.5), 0.5)
+    curves = [poly, circ]
+    q = np.array([[0.5, 0.5], [0.99, 0.01], [3.0, 0.5], [3.2, 0.6], [1.5, 0.5], [-0.01, 0.5],
+                  [1e3, 1e3], [-1e4, 2.0]])
+    exact = np.array([1, 1, 1, 1, 0, 0, 0, 0], dtype=float)
+    d32, d64, b32, st = _run2(hx, curves, q, beta=8.0)
+    assert np.max(np.abs(d64 - exact)) <= 1e-12
+    assert np.max(np.abs(d32 - exact)) <= 1e-5
+    assert np.max(np.abs(b32 - exact)) <= 1e-4

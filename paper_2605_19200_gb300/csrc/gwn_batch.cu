@@ -47,10 +47,15 @@ struct gwn_batch_s {
 
 namespace {
 
+// field by field: the struct has padding, which callers need not initialise
 bool same_items(const std::vector<gwn_query_item>& a, const gwn_query_item* b, size_t n) {
     if (a.size() != n) return false;
-    for (size_t i = 0; i < n; ++i)
-        if (std::memcmp(&a[i], &b[i], sizeof(gwn_query_item)) != 0) return false;
+    for (size_t i = 0; i < n; ++i) {
+        const gwn_query_item &x = a[i], &y = b[i];
+        if (x.model != y.model || x.points != y.points || x.points_dtype != y.points_dtype || x.n != y.n ||
+            x.out_w != y.out_w || x.out_label != y.out_label || x.out_status != y.out_status)
+            return false;
+    }
     return true;
 }
 

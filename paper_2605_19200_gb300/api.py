@@ -308,6 +308,27 @@ def _stream_handle(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+def _check_shapes(model: Model, pts, out):
+    """The C ABI reads n x dim points and writes n outputs: refuse shapes that
+    would make it read or write past the caller's buffers."""
+    if len(pts.shape) != 2 or pts.shape[1] != model.dim:
+        raise ValueError(f"points must have shape (n, {model.dim})")
+    if out is not None:
+        n = pts.shape[0]
+        for t in out:
+            if t is not None and (len(t.shape) != 1 or t.shape[0] < n):
+                raise ValueError("every output must be 1-D with at least n entries")
+            if t is not None and not (t.is_contiguous() if hasattr(t, "is_contiguous") else t.flags["C_CONTIGUOUS"]):
+                raise ValueError("outputs must be contiguous")
+        w, lab, st = out
+        if str(w.dtype) not in ("float64", "torch.float64"):
+            raise TypeError("out w must be float64")
+        for t in (lab, st):
+            size = None if t is None else (t.element_size() if hasattr(t, "element_size") else t.itemsize)
+            if size is not None and size != 4:
+                raise TypeError("label and status outputs must be 32-bit")
+
+
 def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
               want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
               out=None, beta_leaf: float = 0.0):
@@ -325,6 +346,7 @@ def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, b
         pts = points.contiguous()
         if pts.dtype not in (torch.float32, torch.float64):
             pts = pts.float()
+        _check_shapes(model, pts, out)
         n = pts.shape[0]
         dt = F32 if pts.dtype == torch.float32 else F64
         if out is not None:
@@ -350,6 +372,7 @@ def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, b
         return a.ctypes.data
     if pts.dtype not in (np.float32, np.float64):
         pts = pts.astype(np.float64)
+    _check_shapes(model, pts, out)
     n = pts.shape[0]
     dt = F32 if pts.dtype == np.float32 else F64
     if out is not None:
@@ -379,6 +402,9 @@ def gwn_query_noalloc(model: Model, points, out, stream=None):
     """Query through gwn_query_noalloc: `points` a CUDA tensor (n x dim, float32
     or float64), `out` = (w float64, label int32 or None, status int32 or
     None) CUDA tensors supplied by the caller; the library allocates nothing."""
+    _check_shapes(model, points, out)
+    if str(points.dtype) not in ("torch.float32", "torch.float64") or not points.is_contiguous():
+        raise TypeError("points must be a contiguous float32 or float64 CUDA tensor")
     w, lab, st = out
     dt = F32 if str(points.dtype).endswith("float32") else F64
     _check(lib().gwn_query_noalloc(model.handle, points.data_ptr(), dt, points.shape[0], w.data_ptr(),
@@ -411,6 +437,8 @@ class Server:
         pts = np.ascontiguousarray(points)
         if pts.dtype not in (np.float32, np.float64):
             pts = pts.astype(np.float64)
+        if 0 <= int(model_id) < len(self.dims) and (pts.ndim != 2 or pts.shape[1] != self.dims[int(model_id)]):
+            raise ValueError(f"points must be (n, {self.dims[int(model_id)]}) for model {model_id}")
         rid = ctypes.c_uint64()
         _check(lib().gwn_serve_submit(self.handle, int(model_id), pts.ctypes.data,
                                       F32 if pts.dtype == np.float32 else F64, pts.shape[0], ctypes.byref(rid)))

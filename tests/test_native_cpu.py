@@ -160,3 +160,22 @@ def test_3d_invalid_input_rejected():
     bad_w = G.Patch(1, 1, good.ctrl, -good.weights, good.knots_u, good.knots_v, [])
     with pytest.raises(gwn.GwnError, match="INVALID_GEOMETRY"):
         gwn.gwn_build_3d([bad_w], device=HOST_ONLY)
+
+
+def test_binding_refuses_shapes_that_would_overrun_buffers():
+    """The C ABI reads n x dim points and writes n outputs; the binding refuses
+    arrays whose shapes would make it read or write past them (host path, no GPU)."""
+    import numpy as np
+    import paper_2605_19200_gb300 as gwn
+    from synth import geometry as G
+    m = gwn.gwn_build_2d([G.circle()], device=-2)     # host-only model: no query reaches the device
+    with pytest.raises(ValueError):
+        gwn.gwn_query(m, np.zeros((5, 3)))            # 3 coordinates for a 2D model
+    with pytest.raises(ValueError):
+        gwn.gwn_query(m, np.zeros(10))                # flat array
+    with pytest.raises(ValueError):
+        gwn.gwn_query(m, np.zeros((5, 2)), out=(np.zeros(4), None, None))   # output too short
+    with pytest.raises(TypeError):
+        gwn.gwn_query(m, np.zeros((5, 2)), out=(np.zeros(5, dtype=np.float32), None, None))
+    with pytest.raises(ValueError):
+        gwn.gwn_query(m, np.zeros((5, 2)), out=(np.zeros(10)[::2], None, None))  # strided

@@ -179,3 +179,22 @@ def test_binding_refuses_shapes_that_would_overrun_buffers():
         gwn.gwn_query(m, np.zeros((5, 2)), out=(np.zeros(5, dtype=np.float32), None, None))
     with pytest.raises(ValueError):
         gwn.gwn_query(m, np.zeros((5, 2)), out=(np.zeros(10)[::2], None, None))  # strided
+
+
+def test_shape_checks_accept_the_tensors_the_device_path_passes():
+    """The same checks on torch tensors (as the CUDA path receives them)."""
+    torch = pytest.importorskip("torch")
+    from paper_2605_19200_gb300 import api
+    m = gwn.gwn_build_3d(G.cube_shell(), device=-2)
+    ok = (torch.zeros(5, dtype=torch.float64), torch.zeros(5, dtype=torch.int32), torch.zeros(5, dtype=torch.int32))
+    api._check_shapes(m, torch.zeros((5, 3)), ok)
+    api._check_shapes(m, torch.zeros((5, 3), dtype=torch.float64), (ok[0], None, None))
+    api._check_shapes(m, torch.zeros((0, 3)), None)
+    with pytest.raises(ValueError):
+        api._check_shapes(m, torch.zeros((5, 2)), ok)
+    with pytest.raises(TypeError):
+        api._check_shapes(m, torch.zeros((5, 3)), (torch.zeros(5), None, None))
+    with pytest.raises(TypeError):
+        api._check_shapes(m, torch.zeros((5, 3)), (ok[0], torch.zeros(5, dtype=torch.int64), None))
+    with pytest.raises(ValueError):
+        api._check_shapes(m, torch.zeros((5, 3)), (torch.zeros(10, dtype=torch.float64)[::2], None, None))

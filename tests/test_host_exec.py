@@ -195,3 +195,36 @@ def test_2d_degenerate_and_far_queries(hx, oracle_lib):
     assert np.max(np.abs(d64 - exact)) <= 1e-12
     assert np.max(np.abs(d32 - exact)) <= 1e-5
     assert np.max(np.abs(b32 - exact)) <= 1e-4
+
+
+def test_cubic_and_quadratic_trims(hx, oracle_lib):
+    """Trim loops of degree 3 (composed boundary curves of degree 18) and of
+    degree 2 without weights (degree 12) on a curved bicubic patch: the
+    unrolled degree-18 and degree-12 evaluators against the oracle."""
+    rng = np.random.default_rng(21)
+    # a gently curved bicubic patch over [0, 1]^2
+    u = np.linspace(0, 1, 4)
+    ctrl = np.zeros((4, 4, 3))
+    for i in range(4):
+        for j in range(4):
+            ctrl[i, j] = (u[i], u[j], 0.15 * np.sin(2.0 * u[i]) * np.cos(1.5 * u[j]))
+    def loop(deg, centre, rad, ccw=True):
+        k = 8
+        th = np.linspace(0, 2 * np.pi, k, endpoint=False)
+        pts = np.stack([centre[0] + rad * np.cos(th) * (1 + 0.15 * np.sin(3 * th)),
+                        centre[1] + rad * np.sin(th) * (1 + 0.15 * np.sin(3 * th))], axis=1)
+        pts = np.concatenate([pts, pts[:1]], axis=0)
+        if not ccw:
+            pts = pts[::-1].copy()
+        return G.Curve(deg, pts, np.ones(pts.shape[0]), G.clamped_uniform_knots(pts.shape[0], deg))
+    patches = [G.Patch(3, 3, ctrl, np.ones((4, 4)), G.bezier_knots(3), G.bezier_knots(3),
+                       [loop(3, (0.5, 0.5), 0.3), loop(2, (0.5, 0.5), 0.1, ccw=False)])]
+    q = np.concatenate([rng.uniform(-0.2, 1.2, size=(20, 3)) * [1, 1, 0.5],
+                        np.array([[0.5, 0.72, 0.02], [0.5, 0.72, -0.02], [0.5, 0.5, 0.3], [0.3, 0.45, 0.05]])])
+    q = q.astype(np.float32).astype(np.float64)
+    w_ref, fl = oracle_lib.gwn3d(patches, q)
+    ok = np.isfinite(w_ref)
+    d32, d64, b32, st = _run3(hx, patches, q, beta=8.0, beta_leaf=6.0)
+    assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-7
+    assert np.max(np.abs(d32[ok] - w_ref[ok])) <= 2e-5
+    assert np.max(np.abs(b32[ok] - w_ref[ok])) <= 1e-4

@@ -228,3 +228,38 @@ def test_cubic_and_quadratic_trims(hx, oracle_lib):
     assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-7
     assert np.max(np.abs(d32[ok] - w_ref[ok])) <= 2e-5
     assert np.max(np.abs(b32[ok] - w_ref[ok])) <= 1e-4
+
+
+def _poly15(rng, centre, r):
+    th = np.sort(rng.uniform(0, 2 * np.pi, 15))
+    rad = r * rng.uniform(0.6, 1.0, 15)
+    return G.polyline(np.stack([centre[0] + rad * np.cos(th), centre[1] + rad * np.sin(th)], 1))
+
+
+def test_order0_error_bound_and_overlap_growth(hx, oracle_lib):
+    """Section 4.2: on watertight shapes even the order-0 expansion at beta = 2
+    keeps the error below 0.1, and order 2 is below order 0.  Section 4.3:
+    overlapping closed 15-gons (order 0, beta = 2) raise the absolute error with
+    the number of polygons while the error relative to the GWN stays bounded."""
+    rng = np.random.default_rng(5)
+    g = np.linspace(-1.5, 1.5, 48)
+    q = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2).astype(np.float32).astype(np.float64)
+    polys = [_poly15(rng, (rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)), 1.0) for _ in range(16)]
+    for shape in ([G.circle((0, 0), 1.0)], polys[:1]):
+        w_ref, _ = oracle_lib.gwn2d(shape, q)
+        ok = np.isfinite(w_ref)
+        e = {}
+        for order in (0, 2):
+            _, _, b32, _ = _run2(hx, shape, q, beta=2.0, order=order)
+            e[order] = float(np.max(np.abs(b32[ok] - w_ref[ok])))
+        assert e[0] < 0.1 and e[2] < e[0], e
+    abs_err, rel_err = [], []
+    for k in (1, 4, 16):
+        w_ref, _ = oracle_lib.gwn2d(polys[:k], q)
+        ok = np.isfinite(w_ref)
+        _, _, b32, _ = _run2(hx, polys[:k], q, beta=2.0, order=0)
+        err = np.abs(b32[ok] - w_ref[ok])
+        abs_err.append(float(err.max()))
+        rel_err.append(float((err / np.maximum(1.0, np.abs(w_ref[ok]))).max()))
+    assert abs_err[0] < abs_err[1] < abs_err[2] and abs_err[2] > 2 * abs_err[0], abs_err
+    assert max(rel_err) < 0.3, rel_err

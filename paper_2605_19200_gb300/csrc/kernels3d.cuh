@@ -19,11 +19,12 @@
 //     the two tangential components, and counted if it lies on the half line
 //     and inside the leaf's visible region (winding number of its local 2D
 //     boundary).
-//   The line integral uses 8-point Gauss-Legendre panels, bisected (stackless,
-//   by level and index) until each panel is shorter than PanelRatio times its
-//   distance to q and to the string.  FP32 stops at kLevel32 bisections; a leaf that needs more, or
-//   whose foot point is too close to call in FP32, is evaluated again in FP64:
-//   the near-boundary band.
+//   The line integral uses Gauss-Legendre panels (4 points in FP32, 8 in FP64),
+//   bisected (stackless, by level and index) until each panel is shorter than
+//   a ratio (kRatio*) times its distance to q and to the string.  FP32 stops at
+//   kLevel32 bisections; a leaf that needs more, or whose foot point is too
+//   close to call in FP32, is evaluated again in FP64: the near-boundary band
+//   (one warp per pair, leaf3_warp64).
 // far3: the order-2 Taylor expansion of Eq. 3 in folded form (gwn_internal.h).
 #pragma once
 

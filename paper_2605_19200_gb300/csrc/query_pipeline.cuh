@@ -2,20 +2,23 @@
 //
 //  1. Spatial binning: each point gets the Morton code of its cell in a
 //     2^kBinBits-per-axis grid over the model's box; a counting sort by cell
-//     yields a permutation, so the threads of a warp traverse the tree for
-//     nearby points and take mostly the same branches.
-//  2. Traversal (Algorithm 1): far nodes (and, in 3D, far leaves) add their
-//     Taylor term (Eq. 3) to the point's accumulator.  2D leaves are evaluated
-//     in place (one atan2 unless the point is inside the leaf's box).  3D leaves
-//     that need the exact evaluation are not evaluated in the traversal: the
-//     (point, leaf) pair is appended to a work list, with one atomic per warp.
+//     yields a permutation, so the 32 points of a warp are neighbours.
+//  2. Traversal (Algorithm 1), one packet per warp: the warp's points walk the
+//     tree together; far nodes (and, in 3D, far leaves) add their Taylor term
+//     (Eq. 3) to each point's accumulator.  2D leaves are evaluated in place
+//     (one atan2 unless the point is inside the leaf's box).  3D leaves that
+//     need the exact evaluation are not evaluated in the traversal: the
+//     (point, leaf) pair is appended to a work list, with one atomic per warp;
+//     points whose pairs do not fit are traversed again in up to two more
+//     rounds.
 //  3. 3D only: the work list is counting-sorted by leaf, and one thread per pair
-//     evaluates the leaf and adds it to the point's accumulator.  Consecutive
-//     threads now share the same leaf, so a warp reads one set of boundary
-//     curves and runs the same quadrature panels.
+//     evaluates the leaf in FP32 and adds it to the point's accumulator.
+//     Consecutive threads now share the same leaf, so a warp reads one set of
+//     boundary curves and runs mostly the same quadrature panels.  Pairs FP32
+//     cannot resolve go to the FP64 near band (one warp per pair).
 //  4. Finish: value, label and status per point; points whose value lies within
 //     the repair band of a half-integer, or that were flagged, are appended to
-//     the FP64 repair list.
+//     the FP64 repair list (warp traversal + FP64 pairs, one warp per pair).
 #pragma once
 
 #include "gwn_internal.h"

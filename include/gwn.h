@@ -236,6 +236,20 @@ gwn_status gwn_model_leaves(gwn_model model, int64_t* prim, double* param);
  * Any pointer may be NULL. */
 gwn_status gwn_model_tree(gwn_model model, int32_t* child, double* x0, double* r, double* mom);
 
+/* Checkpoint: write a built model (its host arrays: tree, moments, leaf
+ * geometry, and its build options after autotuning) to `path`, so that a
+ * serving process can restore it with gwn_model_load instead of rebuilding
+ * (the paper has no counterpart).  Errors: INVALID_ARG (cannot open),
+ * INTERNAL (write failed). */
+gwn_status gwn_model_save(gwn_model model, const char* path);
+
+/* Read a model written by gwn_model_save and upload it to `device` (-1 =
+ * current, GWN_DEVICE_HOST_ONLY = host copy only).  A model saved from a
+ * host-only build with beta = 0 is autotuned on load.  Errors: INVALID_ARG
+ * (cannot open, not a model file of this library version, inconsistent
+ * arrays), OOM, CUDA. */
+gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out);
+
 /* ---------------------------------------------------------------- batches
  * Many models and point sets in one launch.  Algorithm 1 is stated for one
  * model; a batch runs the query of each item (its own model, points and

@@ -10,6 +10,7 @@ number itself.
 from __future__ import annotations
 
 import ctypes
+import os
 from typing import Optional, Sequence
 
 import numpy as np
@@ -96,6 +97,8 @@ _SIGS = {
     "gwn_model_leaves": (ctypes.c_int, [_P, _P, _P]),
     "gwn_model_tree": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gwn_release": (ctypes.c_int, [_P]),
+    "gwn_model_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "gwn_model_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(_P)]),
     "gwn_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
     "gwn_query_batch": (ctypes.c_int, [_P, ctypes.POINTER(gwn_query_item), ctypes.c_size_t, _P]),
     "gwn_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -392,6 +395,20 @@ def gwn_model_info(model: Model) -> dict:
 
 def gwn_release(model: Model):
     model.release()
+
+
+def gwn_model_save(model: Model, path: str):
+    """Write a built model to `path` (gwn_model_load restores it without rebuilding)."""
+    _check(lib().gwn_model_save(model.handle, os.fsencode(path)))
+
+
+def gwn_model_load(path: str, device: int = -1) -> Model:
+    """Restore a model written by gwn_model_save (device -2: host copy only)."""
+    h = ctypes.c_void_p()
+    _check(lib().gwn_model_load(os.fsencode(path), int(device), ctypes.byref(h)))
+    m = Model(h.value, 0)
+    m.dim = m.info()["dim"]
+    return m
 
 
 def gwn_version() -> str:

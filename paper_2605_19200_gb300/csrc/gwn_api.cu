@@ -1043,6 +1043,132 @@ gwn_status gwn_model_tree(gwn_model m, int32_t* child, double* x0, double* r, do
     return GWN_OK;
 }
 
+// ---------------------------------------------------------------- checkpoint
+//
+// A model file holds everything the device upload needs, so that a serving
+// process can load a model without rebuilding it: a header (magic, format
+// version, dimension, leaf mode, primitive count, build options after
+// autotuning) and every host array of the model, each as a 64-bit element
+// count followed by the raw elements.  Files are written and read on
+// little-endian hosts (x86-64, aarch64) with the same struct layouts.
+
+}  // extern "C"
+
+namespace {
+constexpr char kModelMagic[8] = {'G', 'W', 'N', 'M', 'O', 'D', 'E', 'L'};
+constexpr uint32_t kModelVersion = 1;
+
+template <typename V>
+bool write_vec(FILE* f, const std::vector<V>& v) {
+    const uint64_t n = v.size();
+    return std::fwrite(&n, sizeof(n), 1, f) == 1 && (n == 0 || std::fwrite(v.data(), sizeof(V), n, f) == n);
+}
+
+template <typename V>
+bool read_vec(FILE* f, std::vector<V>* v, uint64_t max_elems) {
+    uint64_t n = 0;
+    if (std::fread(&n, sizeof(n), 1, f) != 1 || n > max_elems) return false;
+    v->resize((size_t)n);
+    return n == 0 || std::fread(v->data(), sizeof(V), (size_t)n, f) == n;
+}
+
+// apply f to every array of the host model, in file order
+template <typename F>
+bool each_array(HostModel& H, F f) {
+    return f(H.child) && f(H.hdr) && f(H.mom) && f(H.hdr64) && f(H.mom64) && f(H.lhdr) && f(H.lmom) &&
+           f(H.lhdr64) && f(H.lmom64) && f(H.x0) && f(H.r) && f(H.mom_c) && f(H.leaf_prim) && f(H.leaf_param) &&
+           f(H.leaf2) && f(H.leaf2_64) && f(H.leaf3) && f(H.net3) && f(H.net3_64) && f(H.c3) && f(H.c3pts) &&
+           f(H.c3pts64) && f(H.c2) && f(H.c2_64) && f(H.c2mult);
+}
+}  // namespace
+
+extern "C" {
+
+gwn_status gwn_model_save(gwn_model m, const char* path) {
+    if (!m || !path) return fail(GWN_ERR_INVALID_ARG, "model and path are required");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(GWN_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
+    const int32_t hdr[4] = {(int32_t)kModelVersion, m->dim, m->leaf_far, (int32_t)sizeof(gwn_build_opts)};
+    const HostModel& H = m->host;
+    const int32_t hm[3] = {H.dim, H.n_leaves, H.max_depth};
+    bool ok = std::fwrite(kModelMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
+              std::fwrite(&m->opts, sizeof(gwn_build_opts), 1, f) == 1 && std::fwrite(hm, sizeof(hm), 1, f) == 1 &&
+              std::fwrite(H.lo, sizeof(H.lo), 1, f) == 1 && std::fwrite(H.hi, sizeof(H.hi), 1, f) == 1 &&
+              each_array(const_cast<HostModel&>(H), [&](auto& v) { return write_vec(f, v); });
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? GWN_OK : fail(GWN_ERR_INTERNAL, std::string("write failed: ") + path);
+}
+
+gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
+    if (!path || !out) return fail(GWN_ERR_INVALID_ARG, "path and out are required");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(GWN_ERR_INVALID_ARG, std::string("cannot open for reading: ") + path);
+    gwn_model_s* m = new (std::nothrow) gwn_model_s();
+    if (!m) {
+        std::fclose(f);
+        return fail(GWN_ERR_OOM, "host allocation failed");
+    }
+    char magic[8] = {};
+    int32_t hdr[4] = {}, hm[3] = {};
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kModelMagic, 8) == 0 &&
+              std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == (int32_t)kModelVersion &&
+              (hdr[1] == 2 || hdr[1] == 3) && hdr[3] == (int32_t)sizeof(gwn_build_opts) &&
+              std::fread(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
+              std::fread(&m->opts, sizeof(gwn_build_opts), 1, f) == 1 && std::fread(hm, sizeof(hm), 1, f) == 1 &&
+              std::fread(m->host.lo, sizeof(m->host.lo), 1, f) == 1 &&
+              std::fread(m->host.hi, sizeof(m->host.hi), 1, f) == 1;
+    try {
+        // no array may hold more elements than the file has bytes
+        const uint64_t cap = (uint64_t)1 << 36;
+        ok = ok && each_array(m->host, [&](auto& v) { return read_vec(f, &v, cap); });
+    } catch (const std::bad_alloc&) {
+        ok = false;
+    }
+    std::fclose(f);
+    HostModel& H = m->host;
+    if (ok) {
+        m->dim = hdr[1];
+        m->leaf_far = hdr[2] ? 1 : 0;
+        H.dim = hm[0];
+        H.n_leaves = hm[1];
+        H.max_depth = hm[2];
+        // consistency of the arrays the kernels index
+        const size_t nl = (size_t)H.n_leaves, ni = nl > 0 ? nl - 1 : 0;
+        ok = H.dim == m->dim && H.n_leaves >= 1 && H.child.size() == ni && H.hdr.size() == ni &&
+             H.lhdr.size() == nl && H.leaf_prim.size() == nl &&
+             (m->dim == 2 ? H.leaf2.size() == nl * kLeaf2Vec : H.leaf3.size() == nl);
+    }
+    if (!ok || check_opts(m->opts) != GWN_OK) {
+        delete m;
+        return fail(GWN_ERR_INVALID_ARG, std::string("not a model file of this library version: ") + path);
+    }
+    m->opts.device = device;
+    if (device == GWN_DEVICE_HOST_ONLY) {
+        m->device = GWN_DEVICE_HOST_ONLY;
+        *out = m;
+        return GWN_OK;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    DeviceGuard g(device);
+    cudaGetDevice(&m->device);
+    const bool tune = m->opts.beta == 0.0;  // saved from a host-only build: tune now
+    if (tune) m->opts.beta = 2.0;
+    gwn_status s = finish_build(m, out);
+    if (s != GWN_OK) return s;
+    if (tune) {
+        s = autotune(m);
+        if (s != GWN_OK) {
+            gwn_release(m);
+            *out = nullptr;
+            return s;
+        }
+    }
+    m->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return GWN_OK;
+}
+
 gwn_status gwn_release(gwn_model m) {
     if (!m) return GWN_OK;
     if (m->device != GWN_DEVICE_HOST_ONLY) {

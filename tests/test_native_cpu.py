@@ -198,3 +198,48 @@ def test_shape_checks_accept_the_tensors_the_device_path_passes():
         api._check_shapes(m, torch.zeros((5, 3)), (ok[0], torch.zeros(5, dtype=torch.int64), None))
     with pytest.raises(ValueError):
         api._check_shapes(m, torch.zeros((5, 3)), (torch.zeros(10, dtype=torch.float64)[::2], None, None))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_model_checkpoint_roundtrip(tmp_path, dim):
+    """gwn_model_save / gwn_model_load restore every host array and option of a
+    model bit for bit (host copies; the device upload is the build's own)."""
+    if dim == 2:
+        curves, _ = configs.star_2d(n_queries=4)
+        m = gwn.gwn_build_2d(curves, beta=6.0, device=-2)
+    else:
+        patches, _ = configs.cad_3d(31, 80, 0)
+        m = gwn.gwn_build_3d(patches, beta=6.0, beta_leaf=4.0, adaptive_beta=1, device=-2)
+    path = str(tmp_path / "model.gwn")
+    gwn.gwn_model_save(m, path)
+    r = gwn.gwn_model_load(path, device=-2)
+    a, b = m.info(), r.info()
+    for k in ("dim", "n_primitives", "n_leaves", "n_nodes", "max_depth", "beta", "beta_leaf", "order",
+              "repair_band", "beta_repair"):
+        assert a[k] == b[k], k
+    ta, tb = m.tree(), r.tree()
+    for k in ("child", "x0", "r", "mom"):
+        assert ta[k].size > 0 and np.array_equal(ta[k], tb[k]), k
+    pa, qa = m.leaves()
+    pb, qb = r.leaves()
+    assert np.array_equal(pa, pb) and np.array_equal(qa, qb)
+    # every array (leaf geometry, boundary curves, FP64 copies) survives: the
+    # restored model writes the same bytes
+    again = str(tmp_path / "again.gwn")
+    gwn.gwn_model_save(r, again)
+    assert open(path, "rb").read() == open(again, "rb").read()
+
+
+def test_model_load_rejects_bad_files(tmp_path):
+    curves, _ = configs.star_2d(n_queries=4)
+    m = gwn.gwn_build_2d(curves, beta=6.0, device=-2)
+    good = tmp_path / "m.gwn"
+    gwn.gwn_model_save(m, str(good))
+    data = good.read_bytes()
+    for name, blob in (("magic", b"XXXXXXXX" + data[8:]), ("truncated", data[: len(data) // 2]), ("empty", b"")):
+        p = tmp_path / (name + ".gwn")
+        p.write_bytes(blob)
+        with pytest.raises(gwn.GwnError):
+            gwn.gwn_model_load(str(p), device=-2)
+    with pytest.raises(gwn.GwnError):
+        gwn.gwn_model_load(str(tmp_path / "missing.gwn"), device=-2)

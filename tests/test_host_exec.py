@@ -263,3 +263,19 @@ def test_order0_error_bound_and_overlap_growth(hx, oracle_lib):
         rel_err.append(float((err / np.maximum(1.0, np.abs(w_ref[ok]))).max()))
     assert abs_err[0] < abs_err[1] < abs_err[2] and abs_err[2] > 2 * abs_err[0], abs_err
     assert max(rel_err) < 0.3, rel_err
+
+
+def test_2d_near_curve_uses_the_fp64_band(hx):
+    """Points 1e-5 and 1e-3 off a rational circle and off a cubic Bezier chain:
+    the FP32 bisection gives up near the curve and the FP64 band decides; the
+    values stay at the exact 0 / 1 of the closed circle."""
+    circ = [G.circle((0.2, -0.1), 0.8)]
+    th = np.linspace(0, 2 * np.pi, 24, endpoint=False)
+    rs = np.array([1 - 1e-3, 1 - 1e-5, 1 + 1e-5, 1 + 1e-3])
+    q = np.concatenate([np.stack([0.2 + 0.8 * r * np.cos(th), -0.1 + 0.8 * r * np.sin(th)], 1) for r in rs])
+    exact = np.repeat((rs < 1).astype(float), th.size)
+    d32, d64, b32, st = _run2(hx, circ, q, beta=8.0)
+    assert np.max(np.abs(d64 - exact)) <= 1e-10
+    assert np.max(np.abs(d32 - exact)) <= 1e-5
+    assert np.max(np.abs(b32 - exact)) <= 1e-4
+    assert np.any(st & api.QS_NEAR)

@@ -279,3 +279,19 @@ def test_2d_near_curve_uses_the_fp64_band(hx):
     assert np.max(np.abs(d32 - exact)) <= 1e-5
     assert np.max(np.abs(b32 - exact)) <= 1e-4
     assert np.any(st & api.QS_NEAR)
+
+
+def test_moment_quadrature_points(hx, oracle_lib):
+    """Section 4.2's quadrature study (n = 1..10 Gauss-Legendre points for the
+    3D moments): on subdivided CAD leaves the moments have converged by n = 5,
+    so the traversal's error with 5 and 10 points is the same, and even 2
+    points keep it within a few 1e-4."""
+    patches, q = configs.cad_3d(1234, 120, 60)
+    w_ref, _ = oracle_lib.gwn3d(patches, q)
+    ok = np.isfinite(w_ref)
+    err = {}
+    for n in (2, 5, 10):
+        _, _, b32, _ = _run3(hx, patches, q, beta=6.0, beta_leaf=4.0, quad_nodes=n)
+        err[n] = float(np.max(np.abs(b32[ok] - w_ref[ok])))
+    assert abs(err[5] - err[10]) <= 1e-6, err
+    assert err[10] <= 1e-4 and err[2] <= 5e-4, err

@@ -246,6 +246,58 @@ def serving_leg(gwn, phase_s: float, log_fn):
             "slots": 4, "precision": "fp32 bulk + fp64 repair"}
 
 
+def config_leg(config: int, steps: int, warmup: int):
+    """One of the single-model configurations: 1 (2D star, exact FP64), 2 (2D
+    nested loops, 1024^2 grid, FP32 + repair), 3 (trimmed sphere, 1M uniform
+    queries, FP32 + repair).  Times the BVH query and the plain direct sum (on a
+    sample, per-query time extrapolated) with CUDA events; prints one JSON line.
+    Accuracy against the oracle is the GPU tests' job."""
+    import torch
+    import paper_2605_19200_gb300 as gwn
+    from synth import configs
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    if config == 1:
+        prims, q = configs.star_2d()
+        dim, prec, qbeta, kw, direct_n = 2, gwn.PREC_FP64, 1e9, {"beta": 8.0, "precision": gwn.PREC_FP64}, 16384
+        name = "1: 64-curve star, 2D, all FP64 (exact: tree with beta 1e9)"
+    elif config == 2:
+        prims, q = configs.loops_2d()
+        dim, prec, qbeta, kw, direct_n = 2, gwn.PREC_FP32_REPAIR, 0.0, {"beta": 0.0}, 65536
+        name = "2: 200 loops, 19,000 curves, 1024^2 grid, FP32 bulk + FP64 repair"
+    else:
+        prims, q = configs.sphere_3d()
+        dim, prec, qbeta, kw, direct_n = 3, gwn.PREC_FP32_REPAIR, 0.0, {"beta": 0.0}, 65536
+        name = "3: trimmed sphere, 384 patches, 1M uniform queries, FP32 bulk + FP64 repair"
+    build = gwn.gwn_build_2d if dim == 2 else gwn.gwn_build_3d
+    m = build(prims, **kw)
+    md = build(prims, max_aabb_frac=0.0)
+    pts = torch.from_numpy(q).to(torch.float64 if prec == gwn.PREC_FP64 else torch.float32).to(dev).contiguous()
+
+    def timed(model, p, mode, beta):
+        n = p.shape[0]
+        out = (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.int32, device=dev), None)
+        for _ in range(max(1, warmup)):
+            model.query(p, precision=prec, mode=mode, beta=beta, out=out, stream=stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            model.query(p, precision=prec, mode=mode, beta=beta, out=out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return n * steps / (a.elapsed_time(b) / 1e3)
+
+    qps = timed(m, pts, gwn.MODE_BVH, qbeta)
+    dqps = timed(md, pts[:direct_n].contiguous(), gwn.MODE_DIRECT, 0.0)
+    info = m.info()
+    print(json.dumps({"metric": "GWN queries/s", "config": name, "value": qps, "unit": "queries/s",
+                      "direct_sum": {"value": dqps, "sample": f"{min(direct_n, pts.shape[0])} queries"},
+                      "speedup": qps / dqps, "beta": info["beta"], "beta_leaf": info["beta_leaf"],
+                      "leaves": info["n_leaves"], "steps": steps}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,9 +315,13 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving phase")
     ap.add_argument("--kernels-only", action="store_true",
                     help="timed steps only (no e2e, direct-sum or CPU legs); for profiler runs")
+    ap.add_argument("--config", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="1-3: time one of the single-model configurations instead of the 16-model workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.config:
+        return config_leg(args.config, args.steps, args.warmup)
 
     import torch
     import torch.distributed as dist

@@ -158,8 +158,9 @@ gwn_status gwn_build_3d(const gwn_patch3d* patches, size_t n, const gwn_build_op
  *   out_w     : n doubles (required); out_label: n int32 = round(w) (nullable);
  *   out_status: n uint32 GWN_QS_* bits (nullable).
  *   stream    : a cudaStream_t, or NULL for the default stream.
- * Concurrent calls on the same model must be serialised by the caller (the
- * model's scratch buffers are shared).  n == 0 is a no-op. */
+ * Calls on the same model share its scratch buffers: each call's work starts
+ * after the previous call's (an event, also across streams), and calls from
+ * several host threads are serialised by the model's lock.  n == 0 is a no-op. */
 gwn_status gwn_query(gwn_model model, const void* points, int32_t points_dtype, int32_t mem, size_t n,
                      double* out_w, int32_t* out_label, uint32_t* out_status, const gwn_query_opts* qopts,
                      void* stream);

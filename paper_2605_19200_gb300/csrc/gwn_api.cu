@@ -90,6 +90,9 @@ void free_model_memory(gwn_model_s* m) {
     for (auto& row : m->ev)
         for (auto& e : row)
             if (e) cudaEventDestroy(e), e = nullptr;
+    if (m->last) cudaEventDestroy(m->last);
+    m->last = nullptr;
+    m->last_recorded = false;
     m->ws_mem = nullptr;
     m->ws_bytes = 0;
     m->ws_n = 0;
@@ -843,8 +846,16 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     size_t obytes = n * (sizeof(double) + sizeof(int32_t) + sizeof(uint32_t));
     gwn_status s = ensure_workspace(m, n, mem == GWN_MEM_HOST ? pbytes + obytes + 64 : 0);
     if (s != GWN_OK) return s;
-    if (mem == GWN_MEM_DEVICE)
-        return gwn_enqueue_device(m, points, dtype, n, out_w, out_label, (uint32_t*)out_status, qo, st, m->ws);
+    // calls on other streams share the model's workspace: start after the previous call's work
+    if (!m->last) GWN_CUDA_TRY(cudaEventCreateWithFlags(&m->last, cudaEventDisableTiming));
+    if (m->last_recorded) GWN_CUDA_TRY(cudaStreamWaitEvent(st, m->last, 0));
+    if (mem == GWN_MEM_DEVICE) {
+        s = gwn_enqueue_device(m, points, dtype, n, out_w, out_label, (uint32_t*)out_status, qo, st, m->ws);
+        if (s != GWN_OK) return s;
+        GWN_CUDA_TRY(cudaEventRecord(m->last, st));
+        m->last_recorded = true;
+        return GWN_OK;
+    }
     // host buffers: stage through model-owned device memory
     char* base = reinterpret_cast<char*>(m->stage);
     void* dp = base;
@@ -857,6 +868,8 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     GWN_CUDA_TRY(cudaMemcpyAsync(out_w, dw, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (out_label) GWN_CUDA_TRY(cudaMemcpyAsync(out_label, dl, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     if (out_status) GWN_CUDA_TRY(cudaMemcpyAsync(out_status, ds, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    GWN_CUDA_TRY(cudaEventRecord(m->last, st));
+    m->last_recorded = true;
     GWN_CUDA_TRY(cudaStreamSynchronize(st));
     return GWN_OK;
 }

@@ -35,6 +35,10 @@ struct gwn_model_s {
     bool profiled = false;
     void* stage = nullptr;
     size_t stage_cap = 0;
+    // end of the last gwn_query's work: the next call, possibly on another
+    // stream, waits for it before it reuses the workspace
+    cudaEvent_t last = nullptr;
+    bool last_recorded = false;
 };
 
 // Record an error message for gwn_last_error() and return the status.

@@ -206,6 +206,7 @@ typedef struct {
     int32_t order;
     double lo[3], hi[3];    /* box of all control points */
     double beta_leaf;       /* far-test factor of the leaves (3D; equals beta unless set or tuned) */
+    int32_t device;         /* CUDA ordinal holding the model, or GWN_DEVICE_HOST_ONLY */
 } gwn_model_stats;
 
 gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);

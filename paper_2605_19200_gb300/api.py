@@ -63,7 +63,7 @@ class gwn_model_stats(ctypes.Structure):
                 ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("build_ms", ctypes.c_double), ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double),
                 ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double)]
+                ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double), ("device", ctypes.c_int32)]
 
 
 class gwn_serve_opts(ctypes.Structure):
@@ -332,6 +332,18 @@ def _check_shapes(model: Model, pts, out):
                 raise TypeError("label and status outputs must be 32-bit")
 
 
+def _check_device(model: Model, pts, out):
+    """Device calls hand raw pointers to the kernels: every tensor must be a
+    CUDA tensor on the model's GPU, else the kernels would read host memory or
+    another GPU's memory as if it were their own."""
+    dev = model.info()["device"]
+    for name, t in (("points", pts),) + tuple(("output", t) for t in (out or ()) if t is not None):
+        if not getattr(t, "is_cuda", False):
+            raise TypeError(f"{name} must be a CUDA tensor for a device call")
+        if t.device.index != dev:
+            raise TypeError(f"{name} lives on cuda:{t.device.index}, the model on cuda:{dev}")
+
+
 def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
               want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
               out=None, beta_leaf: float = 0.0):
@@ -350,6 +362,7 @@ def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, b
         if pts.dtype not in (torch.float32, torch.float64):
             pts = pts.float()
         _check_shapes(model, pts, out)
+        _check_device(model, pts, out)
         n = pts.shape[0]
         dt = F32 if pts.dtype == torch.float32 else F64
         if out is not None:
@@ -419,7 +432,10 @@ def gwn_query_noalloc(model: Model, points, out, stream=None):
     """Query through gwn_query_noalloc: `points` a CUDA tensor (n x dim, float32
     or float64), `out` = (w float64, label int32 or None, status int32 or
     None) CUDA tensors supplied by the caller; the library allocates nothing."""
+    if out is None:
+        raise TypeError("gwn_query_noalloc writes into caller-supplied outputs: pass out=(w, label, status)")
     _check_shapes(model, points, out)
+    _check_device(model, points, out)
     if str(points.dtype) not in ("torch.float32", "torch.float64") or not points.is_contiguous():
         raise TypeError("points must be a contiguous float32 or float64 CUDA tensor")
     w, lab, st = out
@@ -514,6 +530,7 @@ class Batch:
             for t in (lab, st):
                 if t is not None and (t.element_size() != 4 or t.shape[0] < p.shape[0]):
                     raise TypeError("label and status outputs must be 32-bit with n entries")
+            _check_device(m, p, o)
             arr[k].model = m.handle.value
             arr[k].points = p.data_ptr()
             arr[k].points_dtype = F32 if str(p.dtype).endswith("float32") else F64

@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <sys/stat.h>
+
 #include "../../include/gwn.h"
 #include "build.h"
 #include "gwn_internal.h"
@@ -849,12 +851,15 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     // calls on other streams share the model's workspace: start after the previous call's work
     if (!m->last) GWN_CUDA_TRY(cudaEventCreateWithFlags(&m->last, cudaEventDisableTiming));
     if (m->last_recorded) GWN_CUDA_TRY(cudaStreamWaitEvent(st, m->last, 0));
+    // the end of whatever this call enqueued, also when a later enqueue fails:
+    // the next call must not reuse the workspace under kernels already queued
+    auto mark_last = [&]() {
+        if (cudaEventRecord(m->last, st) == cudaSuccess) m->last_recorded = true;
+    };
     if (mem == GWN_MEM_DEVICE) {
         s = gwn_enqueue_device(m, points, dtype, n, out_w, out_label, (uint32_t*)out_status, qo, st, m->ws);
-        if (s != GWN_OK) return s;
-        GWN_CUDA_TRY(cudaEventRecord(m->last, st));
-        m->last_recorded = true;
-        return GWN_OK;
+        mark_last();
+        return s;
     }
     // host buffers: stage through model-owned device memory
     char* base = reinterpret_cast<char*>(m->stage);
@@ -864,7 +869,10 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     uint32_t* ds = reinterpret_cast<uint32_t*>(dl + n);
     GWN_CUDA_TRY(cudaMemcpyAsync(dp, points, pbytes, cudaMemcpyHostToDevice, st));
     s = gwn_enqueue_device(m, dp, dtype, n, dw, out_label ? dl : nullptr, out_status ? ds : nullptr, qo, st, m->ws);
-    if (s != GWN_OK) return s;
+    if (s != GWN_OK) {
+        mark_last();
+        return s;
+    }
     GWN_CUDA_TRY(cudaMemcpyAsync(out_w, dw, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (out_label) GWN_CUDA_TRY(cudaMemcpyAsync(out_label, dl, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     if (out_status) GWN_CUDA_TRY(cudaMemcpyAsync(out_status, ds, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -893,8 +901,11 @@ static __device__ __align__(256) int g_noalloc_scratch[kNoAllocHeader + kNoAlloc
 namespace {
 std::mutex g_noalloc_mu;
 int* g_noalloc_addr[256] = {};
+int g_noalloc_sms[256] = {};
 
-gwn_status noalloc_scratch(int dev, int** out) {
+// the array's device address and the device's SM count, looked up once per
+// device (with that device current) and cached
+gwn_status noalloc_scratch(int dev, int** out, int* sms) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (dev < 0 || dev >= 256) return fail(GWN_ERR_INVALID_ARG, "device ordinal out of range");
     if (!g_noalloc_addr[dev]) {
@@ -902,9 +913,15 @@ gwn_status noalloc_scratch(int dev, int** out) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return fail(GWN_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+        int n_sm = 0;
+        e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || n_sm <= 0)
+            return fail(GWN_ERR_CUDA, std::string("cudaDeviceGetAttribute(SM count): ") + cudaGetErrorString(e));
+        g_noalloc_sms[dev] = n_sm;
         g_noalloc_addr[dev] = reinterpret_cast<int*>(p);
     }
     *out = g_noalloc_addr[dev];
+    *sms = g_noalloc_sms[dev];
     return GWN_OK;
 }
 
@@ -941,7 +958,8 @@ extern "C" gwn_status gwn_query_noalloc(gwn_model m, const void* points, int32_t
                                              " points per call (its scratch array has a fixed size); split the batch");
     DeviceGuard g(m->device);
     int* scratch = nullptr;
-    gwn_status s = noalloc_scratch(m->device, &scratch);
+    int sms = 0;
+    gwn_status s = noalloc_scratch(m->device, &scratch, &sms);
     if (s != GWN_OK) return s;
     int* rcount = scratch;
     int* rlist = scratch + kNoAllocHeader;
@@ -962,9 +980,6 @@ extern "C" gwn_status gwn_query_noalloc(gwn_model m, const void* points, int32_t
     GWN_CUDA_TRY(cudaMemsetAsync(rcount, 0, sizeof(int), st));
     const int B = 128;
     const unsigned nb = (unsigned)((n + B - 1) / B);
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned rb = (unsigned)std::min<long long>(std::max<long long>(nb, sms * 4), (long long)sms * 8);
     if (m->dim == 2) {
         k_query_noalloc<2><<<nb, B, 0, st>>>(m->tree, points, dtype, (long long)n, p, out_w, out_label, out_status, rlist, rcount);
@@ -1031,6 +1046,7 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
         s->hi[k] = m->host.hi[k];
     }
     s->beta_leaf = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
+    s->device = m->device;
     return GWN_OK;
 }
 
@@ -1077,12 +1093,64 @@ bool write_vec(FILE* f, const std::vector<V>& v) {
     return std::fwrite(&n, sizeof(n), 1, f) == 1 && (n == 0 || std::fwrite(v.data(), sizeof(V), n, f) == n);
 }
 
+// reads one array; `left` is the number of bytes of the file not read yet, so a
+// corrupt count can neither allocate more than the file holds nor read past it
 template <typename V>
-bool read_vec(FILE* f, std::vector<V>* v, uint64_t max_elems) {
+bool read_vec(FILE* f, std::vector<V>* v, uint64_t* left) {
     uint64_t n = 0;
-    if (std::fread(&n, sizeof(n), 1, f) != 1 || n > max_elems) return false;
+    if (*left < sizeof(n) || std::fread(&n, sizeof(n), 1, f) != 1) return false;
+    *left -= sizeof(n);
+    if (n > *left / sizeof(V)) return false;
     v->resize((size_t)n);
-    return n == 0 || std::fread(v->data(), sizeof(V), (size_t)n, f) == n;
+    if (n != 0 && std::fread(v->data(), sizeof(V), (size_t)n, f) != n) return false;
+    *left -= n * sizeof(V);
+    return true;
+}
+
+// Every array has the size the build gives it for the model's dimension and
+// leaf count, every child index names a node or a leaf, each node and leaf
+// except the root has exactly one parent (so the traversal ends), and every
+// leaf's and boundary curve's ranges stay inside their tables.
+bool host_model_consistent(const HostModel& H, int dim) {
+    if (H.dim != dim || H.n_leaves < 1) return false;
+    const size_t nl = (size_t)H.n_leaves, ni = nl - 1, d = (size_t)dim;
+    const size_t fv = dim == 2 ? kMom2Vec : kMom3Vec, ff = dim == 2 ? kMom2F64 : kMom3F64;
+    const size_t M = d + d * d + d * d * d;
+    if (H.child.size() != ni || H.hdr.size() != ni || H.mom.size() != ni * fv || H.hdr64.size() != ni * 4 ||
+        H.mom64.size() != ni * ff || H.lhdr.size() != nl || H.lmom.size() != nl * fv || H.lhdr64.size() != nl * 4 ||
+        H.lmom64.size() != nl * ff || H.x0.size() != ni * d || H.r.size() != ni || H.mom_c.size() != ni * M ||
+        H.leaf_prim.size() != nl || H.leaf_param.size() != nl * 4)
+        return false;
+    std::vector<unsigned char> parents(ni + nl, 0);
+    for (size_t k = 0; k < ni; ++k)
+        for (int c : {H.child[k].x, H.child[k].y}) {
+            size_t slot;
+            if (c >= 0) {
+                if ((size_t)c >= ni || c == 0) return false;  // node 0 is the root
+                slot = (size_t)c;
+            } else {
+                const long long li = ~(long long)c;
+                if (li >= (long long)nl) return false;
+                slot = ni + (size_t)li;
+            }
+            if (parents[slot]++) return false;
+        }
+    for (size_t k = 1; k < ni + nl; ++k)
+        if (parents[k] != 1 && !(ni == 0 && k == 0)) return false;
+    if (dim == 2) return H.leaf2.size() == nl * kLeaf2Vec && H.leaf2_64.size() == nl * kLeaf2F64;
+    if (H.leaf3.size() != nl || H.net3.size() != nl * kNet3Vec || H.net3_64.size() != nl * 64 ||
+        H.c3pts64.size() != H.c3pts.size() * 4 || H.c2.size() != H.c2mult.size() * kC2Vec ||
+        H.c2_64.size() != H.c2mult.size() * 12)
+        return false;
+    for (const Curve3Info& c : H.c3)
+        if (c.deg < 1 || c.deg > kMaxC3Deg || c.ctrl_off < 0 ||
+            (size_t)c.ctrl_off + 2 * (2 * (size_t)c.deg + 1) > H.c3pts.size())
+            return false;
+    for (const Leaf3Info& I : H.leaf3)
+        if (I.c3_off < 0 || I.c3_cnt < 0 || (size_t)I.c3_off + (size_t)I.c3_cnt > H.c3.size() || I.c2_off < 0 ||
+            I.c2_cnt < 0 || (size_t)I.c2_off + (size_t)I.c2_cnt > H.c2mult.size())
+            return false;
+    return true;
 }
 
 // apply f to every array of the host model, in file order
@@ -1133,9 +1201,13 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
               std::fread(m->host.lo, sizeof(m->host.lo), 1, f) == 1 &&
               std::fread(m->host.hi, sizeof(m->host.hi), 1, f) == 1;
     try {
-        // no array may hold more elements than the file has bytes
-        const uint64_t cap = (uint64_t)1 << 36;
-        ok = ok && each_array(m->host, [&](auto& v) { return read_vec(f, &v, cap); });
+        // no array may hold more elements than the rest of the file has bytes
+        long pos = ok ? std::ftell(f) : -1;
+        struct stat sb;
+        ok = ok && pos >= 0 && fstat(fileno(f), &sb) == 0 && (uint64_t)sb.st_size >= (uint64_t)pos;
+        uint64_t left = ok ? (uint64_t)sb.st_size - (uint64_t)pos : 0;
+        ok = ok && each_array(m->host, [&](auto& v) { return read_vec(f, &v, &left); });
+        ok = ok && left == 0;  // nothing may follow the last array
     } catch (const std::bad_alloc&) {
         ok = false;
     }
@@ -1148,10 +1220,7 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         H.n_leaves = hm[1];
         H.max_depth = hm[2];
         // consistency of the arrays the kernels index
-        const size_t nl = (size_t)H.n_leaves, ni = nl > 0 ? nl - 1 : 0;
-        ok = H.dim == m->dim && H.n_leaves >= 1 && H.child.size() == ni && H.hdr.size() == ni &&
-             H.lhdr.size() == nl && H.leaf_prim.size() == nl &&
-             (m->dim == 2 ? H.leaf2.size() == nl * kLeaf2Vec : H.leaf3.size() == nl);
+        ok = host_model_consistent(H, m->dim);
     }
     if (!ok || check_opts(m->opts) != GWN_OK) {
         delete m;

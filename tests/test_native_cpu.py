@@ -243,3 +243,120 @@ def test_model_load_rejects_bad_files(tmp_path):
             gwn.gwn_model_load(str(p), device=-2)
     with pytest.raises(gwn.GwnError):
         gwn.gwn_model_load(str(tmp_path / "missing.gwn"), device=-2)
+
+
+# element sizes of the model file's arrays, in file order (gwn_model_save)
+_ARRAY_ELEM = [("child", 8), ("hdr", 16), ("mom", 16), ("hdr64", 8), ("mom64", 8), ("lhdr", 16), ("lmom", 16),
+               ("lhdr64", 8), ("lmom64", 8), ("x0", 8), ("r", 8), ("mom_c", 8), ("leaf_prim", 8),
+               ("leaf_param", 8), ("leaf2", 16), ("leaf2_64", 8), ("leaf3", 48), ("net3", 16), ("net3_64", 8),
+               ("c3", 16), ("c3pts", 16), ("c3pts64", 8), ("c2", 16), ("c2_64", 8), ("c2mult", 4)]
+
+
+def _split_model_file(data):
+    """(header bytes, [(name, count, payload bytes)]) of a model file."""
+    import ctypes
+    from paper_2605_19200_gb300 import api
+    off = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 12 + 48
+    head, arrays = data[:off], []
+    for name, es in _ARRAY_ELEM:
+        n = int(np.frombuffer(data[off:off + 8], dtype=np.uint64)[0])
+        arrays.append((name, n, data[off + 8:off + 8 + n * es]))
+        off += 8 + n * es
+    assert off == len(data)
+    return head, arrays
+
+
+def _join_model_file(head, arrays):
+    out = bytearray(head)
+    for _, n, payload in arrays:
+        out += np.uint64(n).tobytes() + payload
+    return bytes(out)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_model_load_rejects_inconsistent_arrays(tmp_path, dim):
+    """A file whose arrays disagree with the model's leaf count, whose child
+    indices leave the tree, or whose counts exceed the file, is refused before
+    anything reaches a device (the kernels would read out of bounds)."""
+    if dim == 2:
+        curves, _ = configs.star_2d(n_queries=4)
+        m = gwn.gwn_build_2d(curves, beta=6.0, device=-2)
+    else:
+        patches, _ = configs.cad_3d(31, 60, 0)
+        m = gwn.gwn_build_3d(patches, beta=6.0, beta_leaf=4.0, device=-2)
+    good = tmp_path / "m.gwn"
+    gwn.gwn_model_save(m, str(good))
+    data = good.read_bytes()
+    head, arrays = _split_model_file(data)
+    assert _join_model_file(head, arrays) == data
+    idx = {name: k for k, (name, _, _) in enumerate(arrays)}
+    es = dict(_ARRAY_ELEM)
+    bad = {}
+    # one moment block short
+    a = list(arrays)
+    name, n, pl = a[idx["mom"]]
+    a[idx["mom"]] = (name, n - 1, pl[:-es["mom"]])
+    bad["short_mom"] = _join_model_file(head, a)
+    # a child index past the last leaf
+    a = list(arrays)
+    name, n, pl = a[idx["child"]]
+    ch = np.frombuffer(pl, dtype=np.int32).copy()
+    ch[1] = -(m.info()["n_leaves"] + 5)
+    a[idx["child"]] = (name, n, ch.tobytes())
+    bad["child_range"] = _join_model_file(head, a)
+    # a child that points back at the root (the traversal would not end)
+    ch = np.frombuffer(pl, dtype=np.int32).copy()
+    ch[2 * (len(ch) // 2 - 1)] = 0
+    a[idx["child"]] = (name, n, ch.tobytes())
+    bad["child_root"] = _join_model_file(head, a)
+    # a count far beyond the file's size
+    a = list(arrays)
+    name, n, pl = a[idx["r"]]
+    blob = bytearray(_join_model_file(head, a))
+    off = len(head) + sum(8 + len(p) for _, _, p in arrays[:idx["r"]])
+    blob[off:off + 8] = np.uint64(1 << 40).tobytes()
+    bad["huge_count"] = bytes(blob)
+    # bytes after the last array
+    bad["trailing"] = data + b"\0" * 16
+    if dim == 3:
+        # a boundary curve whose points run past the point table
+        a = list(arrays)
+        name, n, pl = a[idx["c3"]]
+        c3 = np.frombuffer(pl, dtype=np.int32).copy().reshape(-1, 4)
+        c3[-1, 0] = len(arrays[idx["c3pts"]][2]) // 16 - 2
+        a[idx["c3"]] = (name, n, c3.tobytes())
+        bad["c3_range"] = _join_model_file(head, a)
+    for key, blob in bad.items():
+        p = tmp_path / (key + ".gwn")
+        p.write_bytes(blob)
+        with pytest.raises(gwn.GwnError, match="INVALID_ARG"):
+            gwn.gwn_model_load(str(p), device=-2)
+    # the unmodified file still loads
+    gwn.gwn_model_load(str(good), device=-2)
+
+
+def test_device_calls_refuse_host_tensors():
+    """A device call hands raw pointers to the kernels: host tensors, or tensors
+    on another GPU, are refused in Python before any query reaches the library."""
+    import torch
+    from paper_2605_19200_gb300 import api
+    curves, _ = configs.star_2d(n_queries=4)
+    m = gwn.gwn_build_2d(curves, beta=6.0, device=-2)
+    pts = torch.zeros((5, 2), dtype=torch.float32)
+    outs = (torch.zeros(5, dtype=torch.float64), None, None)
+    with pytest.raises(TypeError, match="CUDA"):
+        api.gwn_query_noalloc(m, pts, outs)
+    with pytest.raises(TypeError):
+        api.gwn_query_noalloc(m, pts, None)
+
+    class _OnGpu:  # stands in for a CUDA tensor on another device
+        is_cuda = True
+
+        def __init__(self, index):
+            self.device = torch.device("cuda", index)
+
+    with pytest.raises(TypeError, match="CUDA"):
+        api._check_device(m, pts, (torch.zeros(5, dtype=torch.float64), None, None))
+    # the host-only model lives on no GPU: any device index is another GPU's
+    with pytest.raises(TypeError, match="lives on"):
+        api._check_device(m, _OnGpu(3), None)

@@ -484,13 +484,32 @@ GWN_HD int leaf_hit(const DevTree& t, const Leaf3Info& I, const G& g, const T q[
     return kHitOk;
 }
 
+// the leaf's mean normal as a unit vector in precision T.  It is stored in
+// float, so in double it is a unit vector only to ~6e-8; the string potential
+// A_s has curl r / |r|^3 only for |s| = 1, and a string of length 1 + e shifts
+// the line integral by about e times the leaf's solid angle, so the FP64
+// evaluations renormalise it in double
+template <typename T>
+GWN_HD inline void unit_normal(const Leaf3Info& I, T nrm[3]) {
+    nrm[0] = (T)I.nrm[0];
+    nrm[1] = (T)I.nrm[1];
+    nrm[2] = (T)I.nrm[2];
+    if (sizeof(T) == 8) {
+        const T l = T(1) / sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        nrm[0] *= l;
+        nrm[1] *= l;
+        nrm[2] *= l;
+    }
+}
+
 // GWN of leaf li at q (q relative to the leaf geometry's origin); false if the
 // precision of T could not resolve it
 template <typename T, typename G>
 GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T q[3], T* out, int maxlevel, T ratio,
                        WorkLocal* wl = nullptr) {
     if (wl) wl->v[kWorkLeaves] += 1;
-    T nrm[3] = {(T)I.nrm[0], (T)I.nrm[1], (T)I.nrm[2]};
+    T nrm[3];
+    unit_normal<T>(I, nrm);
     T cen[3];
     if (sizeof(T) == 4) {
         cen[0] = cen[1] = cen[2] = T(0);
@@ -577,7 +596,8 @@ __device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3],
     const int lane = threadIdx.x & 31, grp = lane / K, k = lane % K;
     const Leaf3Info I = t.leaf3[li];
     const Geo64 g{t.net3_64 + (size_t)li * 64, nullptr};
-    const double nrm[3] = {(double)I.nrm[0], (double)I.nrm[1], (double)I.nrm[2]};
+    double nrm[3];
+    unit_normal<double>(I, nrm);
     const double dq[3] = {q[0] - (double)I.cen[0], q[1] - (double)I.cen[1], q[2] - (double)I.cen[2]};
     const double d2 = dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2];
     const double rfar = 1.1 * (double)I.rad;

@@ -89,7 +89,7 @@ def test_3d_leaf_evaluators_and_traversal(hx, oracle_lib, shape):
     w_ref, fl = oracle_lib.gwn3d(patches, q, near_thr=1e-6 * _diag3(patches))
     ok = np.isfinite(w_ref)
     d32, d64, b32, st = _run3(hx, patches, q, beta=6.0, beta_leaf=4.0)
-    assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-7     # all-FP64 exact evaluation
+    assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-9     # all-FP64 exact evaluation
     assert np.max(np.abs(d32[ok] - w_ref[ok])) <= 2e-5     # FP32 quadrature + FP64 near band
     assert np.max(np.abs(b32[ok] - w_ref[ok])) <= 1e-4     # FP32 traversal, order-2 far field
     assert not np.any(st & api.QS_UNRESOLVED)
@@ -103,7 +103,7 @@ def test_3d_near_surface_uses_the_fp64_band(hx, oracle_lib):
     q = np.stack([np.full_like(hs, 0.05), np.full_like(hs, -0.02), hs], axis=1).astype(np.float32).astype(np.float64)
     w_ref, _ = oracle_lib.gwn3d([disk], q)
     d32, d64, b32, st = _run3(hx, [disk], q, beta=6.0, beta_leaf=4.0, max_aabb_frac=0.0)
-    assert np.max(np.abs(d64 - w_ref)) <= 1e-8
+    assert np.max(np.abs(d64 - w_ref)) <= 1e-9
     assert np.max(np.abs(d32 - w_ref)) <= 1e-5
     assert np.any(st & api.QS_NEAR)                      # the band was used
 
@@ -295,3 +295,32 @@ def test_moment_quadrature_points(hx, oracle_lib):
         err[n] = float(np.max(np.abs(b32[ok] - w_ref[ok])))
     assert abs(err[5] - err[10]) <= 1e-6, err
     assert err[10] <= 1e-4 and err[2] <= 5e-4, err
+
+
+@pytest.mark.parametrize("shape", ["cad", "sphere"])
+def test_3d_fp64_near_surface_matches_oracle(hx, oracle_lib, shape):
+    """Queries 1e-1 .. 1e-5 off the surface, both sides, where the leaf takes the
+    string along its mean normal: the FP64 evaluation holds 1e-9 against the
+    oracle (the string must be a unit vector in FP64, not only in float)."""
+    from tests import refgeom as R
+    if shape == "cad":
+        patches, _ = configs.cad_3d(1234, 120, 4)
+    else:
+        patches, _ = configs.sphere_3d(n_queries=4)
+    rng = np.random.default_rng(5)
+    pts = []
+    for k in rng.choice(len(patches), size=6, replace=False):
+        p = patches[k]
+        c = p.trims[0].ctrl[:-1].mean(axis=0)
+        uv = np.clip(c + 0.1 * rng.uniform(-1, 1, size=(2, 2)), 0.01, 0.99)
+        S, Su, Sv = R.surface_point_derivs(p, uv[:, 0], uv[:, 1])
+        n = np.cross(Su, Sv)
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        for h in (1e-1, 1e-3, 1e-5):
+            pts += [S + h * n, S - h * n]
+    q = np.concatenate(pts)
+    w_ref, fl = oracle_lib.gwn3d(patches, q)
+    ok = np.isfinite(w_ref)
+    d32, d64, b32, st = _run3(hx, patches, q, beta=6.0, beta_leaf=4.0)
+    assert np.max(np.abs(d64[ok] - w_ref[ok])) <= 1e-9
+    assert not np.any(st & api.QS_UNRESOLVED)

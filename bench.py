@@ -8,7 +8,13 @@ log-uniform in [65,536, 4,194,304] per model, uniform in each model's box --
 the synthetic stand-in for the paper's CAD collection (Section 4.4).  One
 step queries every model once (FP32 bulk with FP64 repair, beta chosen to meet
 max |dGWN| <= 1e-4).  value = queries/s with points already on the device;
-e2e = the same through the C ABI with pinned host buffers, copies included.
+e2e = the same through the C ABI's host-buffer batch call
+(gwn_query_batch_host: pinned host points in, values and labels out, copies
+inside the timed region).  accuracy = the step's outputs against the exact
+direct sum on the GPU (65,536 seeded queries per model) and, in the CPU leg,
+against the FP64 oracle on the queries the GPU flagged plus seeded ones.  The
+default run also measures configurations 1-3 (other_configs) and the serving
+loop (serving).
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl gwn|reference]
 
@@ -39,10 +45,19 @@ import numpy as np
 
 BETA = 0.0              # 0: the build's autotuner picks beta and beta_leaf per model for max |dGWN| <= 1e-4
 DIRECT_SAMPLE = 40960   # queries per model for the plain direct-sum comparison (fills the GPU)
-ORACLE_SAMPLE = 3       # queries per model for the CPU oracle (about 10 s on 16 cores)
+ORACLE_FLAGGED = 2      # queries per model that the GPU flagged (repaired / near band) for the CPU oracle
+ORACLE_SEEDED = 1       # seeded queries per model for the CPU oracle (about 10-20 s in all on 16 cores)
+ORACLE_SEED = 4242
+ACCURACY_SAMPLE = 65536  # seeded queries per model compared with the exact GPU direct sum
+ACCURACY_SEED = 2026
 WORKLOAD_NAME = ("cad16: 16 models of trimmed bicubic rational patches (box/cylinder unions), "
                  "queries uniform in each model's box")
 PAIR_EVAL_DRAM_BYTES_PER_PAIR = 10.5  # ncu dram__bytes_read + dram__bytes_write of k_pair_eval per pair
+
+
+def patches_box(patches):
+    pts = np.concatenate([p.ctrl.reshape(-1, 3) for p in patches], axis=0)
+    return pts.min(axis=0), pts.max(axis=0)
 
 
 def build_workload(scale_queries: float = 1.0, n_models: int = 16):
@@ -246,14 +261,16 @@ def serving_leg(gwn, phase_s: float, log_fn):
             "slots": 4, "precision": "fp32 bulk + fp64 repair"}
 
 
-def config_leg(config: int, steps: int, warmup: int):
+def config_leg(config: int, steps: int, warmup: int) -> dict:
     """One of the single-model configurations: 1 (2D star, exact FP64), 2 (2D
     nested loops, 1024^2 grid, FP32 + repair), 3 (trimmed sphere, 1M uniform
     queries, FP32 + repair).  Times the BVH query and the plain direct sum (on a
-    sample, per-query time extrapolated) with CUDA events; prints one JSON line.
-    Accuracy against the oracle is the GPU tests' job."""
+    sample, per-query time extrapolated) with CUDA events, and checks every
+    query's value and label against the exact direct sum on the GPU (config 1:
+    the FP64 direct sum; configs 2 and 3: the accuracy module's reference)."""
     import torch
     import paper_2605_19200_gb300 as gwn
+    from paper_2605_19200_gb300 import accuracy
     from synth import configs
 
     dev = torch.device("cuda", 0)
@@ -272,7 +289,7 @@ def config_leg(config: int, steps: int, warmup: int):
         name = "3: trimmed sphere, 384 patches, 1M uniform queries, FP32 bulk + FP64 repair"
     build = gwn.gwn_build_2d if dim == 2 else gwn.gwn_build_3d
     m = build(prims, **kw)
-    md = build(prims, max_aabb_frac=0.0)
+    md = accuracy.build_reference(prims, dim)
     pts = torch.from_numpy(q).to(torch.float64 if prec == gwn.PREC_FP64 else torch.float32).to(dev).contiguous()
 
     def timed(model, p, mode, beta):
@@ -287,15 +304,24 @@ def config_leg(config: int, steps: int, warmup: int):
             model.query(p, precision=prec, mode=mode, beta=beta, out=out, stream=stream)
         b.record(stream)
         torch.cuda.synchronize()
-        return n * steps / (a.elapsed_time(b) / 1e3)
+        return n * steps / (a.elapsed_time(b) / 1e3), out
 
-    qps = timed(m, pts, gwn.MODE_BVH, qbeta)
-    dqps = timed(md, pts[:direct_n].contiguous(), gwn.MODE_DIRECT, 0.0)
+    qps, out = timed(m, pts, gwn.MODE_BVH, qbeta)
+    dqps, _ = timed(md, pts[:direct_n].contiguous(), gwn.MODE_DIRECT, 0.0)
+    if config == 1:
+        wr, _, _ = md.query(pts, mode=gwn.MODE_DIRECT, precision=gwn.PREC_FP64, stream=stream)
+        ref_name = "GPU FP64 direct sum over every curve, all 16,384 queries"
+    else:
+        wr, _, _ = accuracy.reference_values(md, pts, stream=stream)
+        ref_name = "exact GPU direct sum (FP32 leaves, FP64 sum, FP64 near half-integers), every query"
+    torch.cuda.synchronize()
+    acc = accuracy.compare(out[0].cpu().numpy(), out[1].cpu().numpy(), wr.cpu().numpy())
+    acc["reference"] = ref_name
     info = m.info()
-    print(json.dumps({"metric": "GWN queries/s", "config": name, "value": qps, "unit": "queries/s",
-                      "direct_sum": {"value": dqps, "sample": f"{min(direct_n, pts.shape[0])} queries"},
-                      "speedup": qps / dqps, "beta": info["beta"], "beta_leaf": info["beta_leaf"],
-                      "leaves": info["n_leaves"], "steps": steps}), flush=True)
+    return {"metric": "GWN queries/s", "config": name, "value": qps, "unit": "queries/s",
+            "direct_sum": {"value": dqps, "sample": f"{min(direct_n, pts.shape[0])} queries"},
+            "speedup": qps / dqps, "beta": info["beta"], "beta_leaf": info["beta_leaf"],
+            "leaves": info["n_leaves"], "steps": steps, "accuracy": acc}
 
 
 def main():
@@ -310,6 +336,7 @@ def main():
     ap.add_argument("--beta", type=float, default=BETA)
     ap.add_argument("--beta-leaf", type=float, default=0.0)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the single-model configurations 1-3")
     ap.add_argument("--streams", type=int, default=4,
                     help="streams of the batched query (one graph launch per step); 0 = one gwn_query per model")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving phase")
@@ -321,7 +348,8 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     if args.config:
-        return config_leg(args.config, args.steps, args.warmup)
+        print(json.dumps(config_leg(args.config, args.steps, args.warmup)), flush=True)
+        return
 
     import torch
     import torch.distributed as dist
@@ -435,44 +463,42 @@ def main():
                 "peak_note": f"FP32 FMA issue: {sms} SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median under load)",
                 "trav_ms_per_step": trav_us / 1e3, "leaf_ms_per_step": leaf_us / 1e3}
 
-    # e2e through the public API with pinned host buffers: every step copies the
-    # points in, runs the query and copies values and labels back (in the timed region)
+    # e2e through the C ABI with host buffers: gwn_query_batch_host copies every
+    # model's points in and its values and labels out (one cudaMemcpyAsync per
+    # buffer on the item's stream, captured with the kernels in the plan's
+    # graph since the buffers are page-locked); timed over the same step count
     host_pts = [p.cpu().pin_memory() for p in points]
     host_out = [(torch.empty(p.shape[0], dtype=torch.float64).pin_memory(),
                  torch.empty(p.shape[0], dtype=torch.int32).pin_memory(), None) for p in points]
-    dev_pts = [torch.empty_like(p) for p in points]
+    hbatch = gwn.Batch(n_streams=max(1, args.streams))
 
     def step_e2e():
-        if batch is not None:
-            for hp, dp in zip(host_pts, dev_pts):
-                dp.copy_(hp, non_blocking=True)
-            batch.query(models, dev_pts, outs, stream=stream)
-            for o, ho in zip(outs, host_out):
-                ho[0].copy_(o[0], non_blocking=True)
-                ho[1].copy_(o[1], non_blocking=True)
-        else:
-            for m, hp, ho in zip(models, host_pts, host_out):
-                gwn.gwn_query(m, hp, out=ho, want_status=False, stream=stream)
+        hbatch.query_host(models, host_pts, host_out, stream=stream)
 
-    step_e2e()
+    for _ in range(max(3, args.warmup)):
+        step_e2e()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t1 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
-    for _ in range(e2e_steps):
+    for _ in range(args.steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t1) / e2e_steps
-    log(f"e2e {e2e_s * 1e3:.1f} ms/step")
+    e2e_s = (time.perf_counter() - t1) / args.steps
+    log(f"e2e {e2e_s * 1e3:.1f} ms/step (gwn_query_batch_host)")
     _, e2e_value = aggregate_ranks(e2e_s * 1e3, total_q, world, dev)
-    h2d = sum(p.numel() * 4 for p in points)
+    h2d = sum(p.numel() * p.element_size() for p in points)
     d2h = sum(p.shape[0] * (8 + 4) for p in points)
+    e2e_match = all(np.array_equal(ho[0].numpy(), o[0].cpu().numpy()) for ho, o in zip(host_out, outs))
+    hbatch.close()
 
-    # plain GPU direct sum on a sample of each model's queries (unsubdivided patches)
-    direct_q, direct_ms = 0, 0.0
-    for (patches, q), p in zip(workload, points):
-        md = gwn.gwn_build_3d(patches, max_aabb_frac=0.0)
+    # plain GPU direct sum (every unsubdivided patch exact) on a sample of each
+    # model's queries; the same model, with a wide FP64 band near half-integers,
+    # is the exact reference of the accuracy check (65,536 seeded queries per model)
+    from paper_2605_19200_gb300 import accuracy
+    direct_q, direct_ms, acc_stats = 0, 0.0, []
+    for mi, ((patches, q), p, o) in enumerate(zip(workload, points, outs)):
+        md = accuracy.build_reference(patches, 3)
         sub = p[:DIRECT_SAMPLE].contiguous()
         md.query(sub, mode=gwn.MODE_DIRECT, stream=stream)
         torch.cuda.synchronize()
@@ -485,20 +511,69 @@ def main():
         # per-query cost is independent of the batch size: extrapolate to the model's queries
         direct_ms += a.elapsed_time(b) * (p.shape[0] / sub.shape[0])
         direct_q += p.shape[0]
+        rng = np.random.default_rng(ACCURACY_SEED + mi)
+        sel = np.sort(rng.choice(p.shape[0], size=min(ACCURACY_SAMPLE, p.shape[0]), replace=False))
+        wr, _, _ = accuracy.reference_values(md, p[torch.from_numpy(sel).to(dev)].contiguous(), stream=stream)
+        torch.cuda.synchronize()
+        acc_stats.append(accuracy.compare(o[0].cpu().numpy()[sel], o[1].cpu().numpy()[sel], wr.cpu().numpy()))
         del md
     direct_qps = direct_q / (direct_ms / 1e3)
-    log(f"direct sum {direct_qps:.3e} q/s")
+    acc = accuracy.merge(acc_stats)
+    acc["reference"] = ("exact GPU direct sum over every unsubdivided patch (FP32 leaves, FP64 sum, FP64 near "
+                        f"band, exact FP64 within {accuracy.REFERENCE_BAND} of half-integers)")
+    acc["sample"] = f"{ACCURACY_SAMPLE} seeded queries per model x {len(models)} models"
+    acc["label_rule"] = "round half away from zero; labels within 1e-6 of a half-integer not compared (Section 4.3)"
+    log(f"direct sum {direct_qps:.3e} q/s; accuracy {acc['max_abs_dgwn']:.2e}, "
+        f"{acc['label_mismatches']} label mismatches of {acc['labels_compared']}")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle (exact FP64 direct sum over every patch, CPU) on the queries
+        # the GPU flagged (repaired or near band: the hardest ones) plus seeded
+        # ones, timed on the host cores and compared with the GPU's values
+        import oracle
         threads = os.cpu_count() or 1
-        nq, dt = run_oracle_sample(workload, ORACLE_SAMPLE, threads)
-        cpu = {"value": nq / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
-               "sample": f"{ORACLE_SAMPLE} queries of each of the 16 models (exact FP64 direct sum), {dt:.1f} s"}
-        if threads > 14:
-            # the paper's CPU figures use 14 threads (one tile of its Xeon): the same sample on 14
-            nq14, dt14 = run_oracle_sample(workload, ORACLE_SAMPLE, 14)
-            cpu["value_14_threads"] = nq14 / dt14
+        flag = gwn.QS_REPAIRED | gwn.QS_NEAR
+        per_model = []
+        for mi, ((patches, q), o) in enumerate(zip(workload, outs)):
+            st = o[2].cpu().numpy()
+            flagged = np.flatnonzero(st & flag)[:ORACLE_FLAGGED]
+            rng = np.random.default_rng(ORACLE_SEED + mi)
+            seeded = rng.choice(q.shape[0], size=ORACLE_SEEDED, replace=False)
+            per_model.append(np.unique(np.concatenate([flagged, seeded])))
+        t0 = time.perf_counter()
+        oracle_w = []
+        for (patches, q), idx in zip(workload, per_model):
+            lo, hi = patches_box(patches)
+            w_o, fl = oracle.gwn3d(patches, q[idx].astype(np.float64), near_thr=1e-6 * float(np.linalg.norm(hi - lo)),
+                                   n_threads=threads)
+            oracle_w.append((w_o, fl))
+        dt = time.perf_counter() - t0
+        nq = sum(len(i) for i in per_model)
+        stats = []
+        for (w_o, fl), idx, o in zip(oracle_w, per_model, outs):
+            ok = (fl & 1) == 0   # labels next to the surface are not unique
+            wg, lg = o[0].cpu().numpy()[idx], o[1].cpu().numpy()[idx]
+            st = accuracy.compare(wg, lg, w_o)
+            # labels are compared away from the surface too (the oracle's near flag)
+            st["label_mismatches"] = int(np.sum((lg != np.round(w_o)) & ok &
+                                                (np.abs(w_o - np.floor(w_o) - 0.5) > 1e-6)))
+            stats.append(st)
+        oc = accuracy.merge(stats)
+        n_flagged = sum(int(np.sum((o[2].cpu().numpy()[idx] & flag) != 0)) for idx, o in zip(per_model, outs))
+        sample = (f"{nq} queries: up to {ORACLE_FLAGGED} per model that the GPU flagged (repaired or near band), "
+                  f"{n_flagged} in all, plus {ORACLE_SEEDED} seeded per model; exact FP64 direct sum, {dt:.1f} s")
+        cpu = {"value": nq / dt, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample}
+        acc["oracle_check"] = {"checked": oc["checked"], "flagged": n_flagged, "max_abs_dgwn": oc["max_abs_dgwn"],
+                               "label_mismatches": oc["label_mismatches"]}
+        log(f"oracle: {nq} queries in {dt:.1f} s, max |dGWN| {oc['max_abs_dgwn']:.2e}")
+
+    other = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        other = []
+        for c in (1, 2, 3):
+            other.append(config_leg(c, max(3, min(args.steps, 10)), 3))
+            log(f"config {c}: {other[-1]['value']:.3e} q/s, accuracy {other[-1]['accuracy']['max_abs_dgwn']:.2e}")
 
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
@@ -521,8 +596,10 @@ def main():
                    "launch": (f"gwn_query_batch: one CUDA graph launch per step over {args.streams} streams"
                               if batch is not None else "one gwn_query per model")},
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "api": "gwn_query_batch_host (pinned host buffers, one graph launch)",
+                "steps": args.steps, "outputs_equal_device_run": bool(e2e_match)},
         "roofline": roofline,
+        "accuracy": acc,
         "direct_sum": {"value": direct_qps, "unit": "queries/s",
                        "sample": f"{DIRECT_SAMPLE} queries per model, FP32, per-query time extrapolated",
                        "speedup": value / direct_qps},
@@ -531,6 +608,8 @@ def main():
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
     }
+    if other is not None:
+        line["other_configs"] = other
     if serving is not None:
         line["serving"] = serving
     if cpu is not None:

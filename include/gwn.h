@@ -132,6 +132,8 @@ typedef struct {
     int32_t count_work; /* 1: count algorithmic work units (slower; see gwn_last_query_stats) */
     int32_t profile;    /* 1: time the traversal and exact-leaf kernels with CUDA events on the stream */
     double beta_leaf;   /* 0 = the model's */
+    double repair_band; /* > 0: re-evaluate in FP64 when |w - round(w) +- 1/2| < this band instead of the
+                           model's (GWN_PREC_FP32_REPAIR only); 0 = the model's (default 0) */
 } gwn_query_opts;
 
 void gwn_default_query_opts(gwn_query_opts* opts);
@@ -285,7 +287,24 @@ gwn_status gwn_batch_create(int32_t n_streams, int32_t device, gwn_batch* out);
  * item), OOM (workspaces), CUDA (capture or launch). */
 gwn_status gwn_query_batch(gwn_batch batch, const gwn_query_item* items, size_t n_items, void* stream);
 
-/* Graph launches so far, graph captures so far, bytes of the stream workspaces. */
+/* The same batch with every item's points and outputs in HOST memory (the
+ * call an application makes when its data lives on the CPU).  For each item
+ * the library copies the points into device memory owned by the plan, runs
+ * the item's query as gwn_query_batch does, and copies the values (and the
+ * labels and status words, when requested) back, with one cudaMemcpyAsync
+ * per buffer on the item's stream, so one item's copies overlap other items'
+ * kernels.  When every host buffer is page-locked (cudaHostAlloc or
+ * cudaHostRegister) the copies are captured with the kernels into the plan's
+ * CUDA graph, and a later call with an identical item list replays it with a
+ * single graph launch; pageable buffers are staged by the CUDA runtime and
+ * the work is issued without a graph.  Synchronous: on return the outputs are
+ * in the caller's host buffers.  The plan keeps device memory for the largest
+ * item list it has staged (points + outputs) until gwn_batch_release.
+ * Errors: as gwn_query_batch; OOM if the staging memory cannot be allocated. */
+gwn_status gwn_query_batch_host(gwn_batch batch, const gwn_query_item* items, size_t n_items, void* stream);
+
+/* Graph launches so far, graph captures so far, bytes of the stream workspaces
+ * and of the staging memory of host items. */
 gwn_status gwn_batch_info(gwn_batch batch, int64_t* graph_launches, int64_t* captures, int64_t* workspace_bytes);
 
 /* Wait for the plan's streams and free it.  NULL is a no-op. */

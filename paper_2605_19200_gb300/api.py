@@ -55,7 +55,8 @@ class gwn_build_opts(ctypes.Structure):
 
 class gwn_query_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double),
-                ("count_work", ctypes.c_int32), ("profile", ctypes.c_int32), ("beta_leaf", ctypes.c_double)]
+                ("count_work", ctypes.c_int32), ("profile", ctypes.c_int32), ("beta_leaf", ctypes.c_double),
+                ("repair_band", ctypes.c_double)]
 
 
 class gwn_model_stats(ctypes.Structure):
@@ -101,6 +102,7 @@ _SIGS = {
     "gwn_model_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(_P)]),
     "gwn_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
     "gwn_query_batch": (ctypes.c_int, [_P, ctypes.POINTER(gwn_query_item), ctypes.c_size_t, _P]),
+    "gwn_query_batch_host": (ctypes.c_int, [_P, ctypes.POINTER(gwn_query_item), ctypes.c_size_t, _P]),
     "gwn_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64)]),
     "gwn_batch_release": (ctypes.c_int, [_P]),
@@ -240,10 +242,10 @@ class Model:
 
     def query(self, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
               want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
-              out=None, beta_leaf: float = 0.0):
+              out=None, beta_leaf: float = 0.0, repair_band: float = 0.0):
         return gwn_query(self, points, mode=mode, precision=precision, beta=beta, stream=stream,
                          want_label=want_label, want_status=want_status, count_work=count_work, profile=profile,
-                         out=out, beta_leaf=beta_leaf)
+                         out=out, beta_leaf=beta_leaf, repair_band=repair_band)
 
 
 def marshal_curves(curves: Sequence):
@@ -346,13 +348,13 @@ def _check_device(model: Model, pts, out):
 
 def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
               want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
-              out=None, beta_leaf: float = 0.0):
+              out=None, beta_leaf: float = 0.0, repair_band: float = 0.0):
     """GWN at points.  torch CUDA tensor -> asynchronous device call with device
     outputs; numpy array or CPU tensor -> host call (staged, synchronous).
     Returns (w float64, label int32 or None, status uint32/int32 or None).
     `out` may supply preallocated outputs (w, label or None, status or None)."""
     q = default_query_opts(mode=mode, precision=precision, beta=beta, count_work=int(count_work),
-                           profile=int(profile), beta_leaf=beta_leaf)
+                           profile=int(profile), beta_leaf=beta_leaf, repair_band=repair_band)
     try:
         import torch
     except Exception:  # pragma: no cover
@@ -540,6 +542,53 @@ class Batch:
             arr[k].out_status = st.data_ptr() if st is not None else None
         self._keep = (list(models), list(points), list(outs))
         _check(lib().gwn_query_batch(self.handle, arr, n, _stream_handle(stream)))
+        return outs
+
+    def query_host(self, models, points, outs, stream=None):
+        """gwn_query_batch_host: points and outputs in host memory (CPU torch
+        tensors or numpy arrays; page-locked buffers let the library capture
+        the copies in its graph).  Synchronous; returns outs."""
+        n = len(models)
+        if not (len(points) == n and len(outs) == n):
+            raise ValueError("models, points and outs must have the same length")
+
+        def _host(a, what):
+            if hasattr(a, "is_cuda") and a.is_cuda:
+                raise TypeError(f"{what} must be in host memory for query_host")
+            if hasattr(a, "is_contiguous"):
+                if not a.is_contiguous():
+                    raise ValueError(f"{what} must be contiguous")
+                return a.data_ptr(), str(a.dtype).replace("torch.", ""), a.element_size(), tuple(a.shape)
+            if not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"{what} must be contiguous")
+            return a.ctypes.data, str(a.dtype), a.itemsize, tuple(a.shape)
+
+        arr = (gwn_query_item * n)()
+        for k, (m, p, o) in enumerate(zip(models, points, outs)):
+            pp, pdt, _, pshape = _host(p, "points")
+            if pdt not in ("float32", "float64") or len(pshape) != 2 or pshape[1] != m.dim:
+                raise TypeError("points must be (n, dim) float32 or float64")
+            w, lab, st = o
+            wp, wdt, _, wshape = _host(w, "out w")
+            if wdt != "float64" or wshape[0] < pshape[0]:
+                raise TypeError("out w must be float64 with n entries")
+            ptrs = []
+            for t in (lab, st):
+                if t is None:
+                    ptrs.append(None)
+                    continue
+                tp, _, es, tshape = _host(t, "label/status output")
+                if es != 4 or tshape[0] < pshape[0]:
+                    raise TypeError("label and status outputs must be 32-bit with n entries")
+                ptrs.append(tp)
+            arr[k].model = m.handle.value
+            arr[k].points = pp
+            arr[k].points_dtype = F32 if pdt == "float32" else F64
+            arr[k].n = pshape[0]
+            arr[k].out_w = wp
+            arr[k].out_label, arr[k].out_status = ptrs
+        self._keep = (list(models), list(points), list(outs))
+        _check(lib().gwn_query_batch_host(self.handle, arr, n, _stream_handle(stream)))
         return outs
 
     def info(self) -> dict:

@@ -252,21 +252,23 @@ __global__ void __launch_bounds__(128) k_query32(DevTree t, const void* pts, int
     double qd[3];
     load_point(pts, dtype, DIM, i, qd);
     uint32_t st = 0;
-    float w = 0.f;
+    // the direct sum adds one FP32 value per leaf (thousands per query): the
+    // running sum is kept in FP64 so that its rounding stays below the leaves' own
+    double wd = 0.0;
     if (DIM == 2) {
         if (p.mode == GWN_MODE_DIRECT) {
-            for (int l = 0; l < t.n_leaves; ++l) w += leaf2_eval32(t, l, (float)qd[0], (float)qd[1], st);
+            for (int l = 0; l < t.n_leaves; ++l) wd += (double)leaf2_eval32(t, l, (float)qd[0], (float)qd[1], st);
         } else {
-            w = query2_32(t, (float)qd[0], (float)qd[1], p.beta2, st);
+            wd = (double)query2_32(t, (float)qd[0], (float)qd[1], p.beta2, st);
         }
     } else {
         if (p.mode == GWN_MODE_DIRECT) {
-            for (int l = 0; l < t.n_leaves; ++l) w += leaf3_eval32(t, l, (float)qd[0], (float)qd[1], (float)qd[2], st);
+            for (int l = 0; l < t.n_leaves; ++l)
+                wd += (double)leaf3_eval32(t, l, (float)qd[0], (float)qd[1], (float)qd[2], st);
         } else {
-            w = query3_32(t, (float)qd[0], (float)qd[1], (float)qd[2], p.beta2, st);
+            wd = (double)query3_32(t, (float)qd[0], (float)qd[1], (float)qd[2], p.beta2, st);
         }
     }
-    double wd = (double)w;
     if (p.precision == GWN_PREC_FP32_REPAIR &&
         (near_half(wd, p.band) || (st & (GWN_QS_STACK_OVERFLOW | GWN_QS_UNRESOLVED)))) {
         int slot = atomicAdd(rcount, 1);
@@ -456,7 +458,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
     // the repair's leaves keep the bulk's ratio beta_leaf / beta
     const double brl = br * beta_leaf / beta;
     p.beta2_repair_leaf = brl > 0 ? brl * brl : 0.0;
-    p.band = (float)m->opts.repair_band;
+    p.band = (float)(qo.repair_band > 0 ? qo.repair_band : m->opts.repair_band);
     p.mode = qo.mode;
     p.precision = qo.precision >= 0 ? qo.precision : m->opts.precision;
     const int B = 128;
@@ -627,6 +629,7 @@ void gwn_default_query_opts(gwn_query_opts* q) {
     q->count_work = 0;
     q->profile = 0;
     q->beta_leaf = 0.0;
+    q->repair_band = 0.0;
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -840,6 +843,7 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     if (qo.precision < -1 || qo.precision > 2) return fail(GWN_ERR_INVALID_ARG, "unknown precision");
     if (qo.beta != 0.0 && !(qo.beta >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta must be >= 2");
     if (qo.beta_leaf != 0.0 && !(qo.beta_leaf >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_leaf must be >= 2");
+    if (!(qo.repair_band >= 0.0 && qo.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
     DeviceGuard g(m->device);
     std::lock_guard<std::mutex> lk(m->mu);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

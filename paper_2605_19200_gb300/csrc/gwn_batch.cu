@@ -38,8 +38,12 @@ struct gwn_batch_s {
     std::vector<gwn::Workspace> ws;
     int ws_leaves = 0;               // workspaces are laid out for this many leaves
     size_t ws_bytes = 0;
+    // device copies of host items' points and outputs (gwn_query_batch_host)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
     // captured graph and the items it was captured for
     std::vector<gwn_query_item> key;
+    bool key_host = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0, captures = 0;
@@ -116,11 +120,13 @@ gwn_status gwn_batch_create(int32_t n_streams, int32_t device, gwn_batch* out) {
     return GWN_OK;
 }
 
-gwn_status gwn_query_batch(gwn_batch B, const gwn_query_item* items, size_t n_items, void* stream) {
-    if (!B) return gwn_fail(GWN_ERR_INVALID_ARG, "batch is NULL");
-    if (n_items == 0) return GWN_OK;
-    if (!items) return gwn_fail(GWN_ERR_INVALID_ARG, "items is NULL");
-    int leaves = 1;
+}  // extern "C"
+
+namespace {
+
+// checks every item against the plan; *leaves receives the largest model's leaf count
+gwn_status check_items(const gwn_batch_s* B, const gwn_query_item* items, size_t n_items, int* leaves) {
+    *leaves = 1;
     for (size_t i = 0; i < n_items; ++i) {
         const gwn_query_item& it = items[i];
         if (!it.model) return gwn_fail(GWN_ERR_INVALID_ARG, "item without a model");
@@ -130,76 +136,188 @@ gwn_status gwn_query_batch(gwn_batch B, const gwn_query_item* items, size_t n_it
         if (it.points_dtype != GWN_F32 && it.points_dtype != GWN_F64)
             return gwn_fail(GWN_ERR_INVALID_ARG, "unknown points dtype");
         if (it.n > (size_t)0x7fffffff) return gwn_fail(GWN_ERR_INVALID_ARG, "at most 2^31 - 1 points per item");
-        leaves = std::max(leaves, it.model->host.n_leaves);
+        *leaves = std::max(*leaves, it.model->host.n_leaves);
     }
-    std::lock_guard<std::mutex> lk(B->mu);
-    int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != B->device) cudaSetDevice(B->device);
-    struct Restore {
-        int d;
-        ~Restore() {
-            if (d >= 0) cudaSetDevice(d);
+    return GWN_OK;
+}
+
+size_t point_bytes(const gwn_query_item& it) {
+    return it.n * (size_t)it.model->dim * (it.points_dtype == GWN_F32 ? sizeof(float) : sizeof(double));
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// device buffers for the points and outputs of host items: `dev` receives the
+// items with their pointers moved into the plan's staging memory
+gwn_status stage_items(gwn_batch_s* B, const gwn_query_item* items, size_t n_items, std::vector<gwn_query_item>* dev) {
+    size_t need = 0;
+    for (size_t i = 0; i < n_items; ++i) {
+        const gwn_query_item& it = items[i];
+        need += align256(point_bytes(it)) + align256(it.n * sizeof(double));
+        if (it.out_label) need += align256(it.n * sizeof(int32_t));
+        if (it.out_status) need += align256(it.n * sizeof(uint32_t));
+    }
+    if (need > B->stage_bytes) {
+        if (B->stage) cudaFree(B->stage);
+        B->stage = nullptr;
+        B->stage_bytes = 0;
+        drop_graph(B);  // a captured graph may point at the old staging memory
+        if (cudaMalloc(&B->stage, std::max<size_t>(need, 256)) != cudaSuccess) {
+            B->stage = nullptr;
+            return gwn_fail(GWN_ERR_OOM, "batch: staging memory for host items");
         }
-    } restore{prev != B->device ? prev : -1};
-    gwn_status s = ensure_workspaces(B, leaves);
+        B->stage_bytes = std::max<size_t>(need, 256);
+    }
+    char* p = reinterpret_cast<char*>(B->stage);
+    dev->assign(items, items + n_items);
+    for (size_t i = 0; i < n_items; ++i) {
+        gwn_query_item& d = (*dev)[i];
+        const gwn_query_item& it = items[i];
+        d.points = p;
+        p += align256(point_bytes(it));
+        d.out_w = reinterpret_cast<double*>(p);
+        p += align256(it.n * sizeof(double));
+        if (it.out_label) {
+            d.out_label = reinterpret_cast<int32_t*>(p);
+            p += align256(it.n * sizeof(int32_t));
+        }
+        if (it.out_status) {
+            d.out_status = reinterpret_cast<uint32_t*>(p);
+            p += align256(it.n * sizeof(uint32_t));
+        }
+    }
+    return GWN_OK;
+}
+
+// Issue the items on the plan's streams: largest item first, each to the least
+// loaded stream; the streams fork from and join into streams[0].  With `host`
+// the items' host buffers are copied in before and out after each query (one
+// cudaMemcpyAsync per buffer on the item's stream); `dev` holds the items as
+// the kernels see them.
+gwn_status issue_plan(gwn_batch_s* B, const gwn_query_item* dev, const gwn_query_item* host, size_t n_items) {
+    std::vector<size_t> order(n_items);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return dev[a].n > dev[b].n; });
+    const size_t ns = B->streams.size();
+    std::vector<double> load(ns, 0.0);
+    std::vector<std::vector<size_t>> plan(ns);
+    for (size_t i : order) {
+        size_t k = std::min_element(load.begin(), load.end()) - load.begin();
+        plan[k].push_back(i);
+        load[k] += (double)dev[i].n + 65536.0;  // fixed cost per item
+    }
+    cudaStream_t origin = B->streams[0];
+    BATCH_CUDA_TRY(cudaEventRecord(B->fork, origin));
+    for (size_t k = 1; k < ns; ++k) BATCH_CUDA_TRY(cudaStreamWaitEvent(B->streams[k], B->fork, 0));
+    gwn_query_opts qo;
+    gwn_default_query_opts(&qo);
+    for (size_t k = 0; k < ns; ++k) {
+        cudaStream_t s = B->streams[k];
+        for (size_t i : plan[k]) {
+            const gwn_query_item& it = dev[i];
+            if (it.n == 0) continue;
+            if (host)
+                BATCH_CUDA_TRY(cudaMemcpyAsync(const_cast<void*>(it.points), host[i].points, point_bytes(it),
+                                               cudaMemcpyHostToDevice, s));
+            gwn_status es = gwn_enqueue_device(it.model, it.points, it.points_dtype, it.n, it.out_w, it.out_label,
+                                               it.out_status, qo, s, B->ws[k]);
+            if (es != GWN_OK) return es;
+            if (host) {
+                BATCH_CUDA_TRY(cudaMemcpyAsync(host[i].out_w, it.out_w, it.n * sizeof(double),
+                                               cudaMemcpyDeviceToHost, s));
+                if (it.out_label)
+                    BATCH_CUDA_TRY(cudaMemcpyAsync(host[i].out_label, it.out_label, it.n * sizeof(int32_t),
+                                                   cudaMemcpyDeviceToHost, s));
+                if (it.out_status)
+                    BATCH_CUDA_TRY(cudaMemcpyAsync(host[i].out_status, it.out_status, it.n * sizeof(uint32_t),
+                                                   cudaMemcpyDeviceToHost, s));
+            }
+        }
+        if (k > 0) {
+            BATCH_CUDA_TRY(cudaEventRecord(B->done[k], s));
+            BATCH_CUDA_TRY(cudaStreamWaitEvent(origin, B->done[k], 0));
+        }
+    }
+    return GWN_OK;
+}
+
+// capture issue_plan into the plan's graph (B->exec) for `key`
+gwn_status capture_plan(gwn_batch_s* B, const gwn_query_item* key, const gwn_query_item* dev,
+                        const gwn_query_item* host, size_t n_items) {
+    drop_graph(B);
+    cudaStream_t cap = B->streams[0];
+    BATCH_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    gwn_status es = issue_plan(B, dev, host, n_items);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cap, &g);
+    if (es != GWN_OK) {
+        if (g) cudaGraphDestroy(g);
+        return es;
+    }
+    if (ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return gwn_fail(GWN_ERR_CUDA, std::string("batch capture failed: ") + cudaGetErrorString(ee));
+    }
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t ce = cudaGraphInstantiate(&ex, g, 0);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return gwn_fail(GWN_ERR_CUDA, std::string("batch graph instantiation failed: ") + cudaGetErrorString(ce));
+    }
+    B->graph = g;
+    B->exec = ex;
+    B->key.assign(key, key + n_items);
+    B->key_host = host != nullptr;
+    B->captures += 1;
+    return GWN_OK;
+}
+
+struct DeviceSwitch {
+    int prev = -1;
+    explicit DeviceSwitch(int dev) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != dev) {
+            prev = cur;
+            cudaSetDevice(dev);
+        }
+    }
+    ~DeviceSwitch() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// page-locked host memory (cudaHostAlloc or cudaHostRegister) can be captured
+// in a graph's copies; pageable memory cannot
+bool page_locked(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+gwn_status gwn_query_batch(gwn_batch B, const gwn_query_item* items, size_t n_items, void* stream) {
+    if (!B) return gwn_fail(GWN_ERR_INVALID_ARG, "batch is NULL");
+    if (n_items == 0) return GWN_OK;
+    if (!items) return gwn_fail(GWN_ERR_INVALID_ARG, "items is NULL");
+    int leaves = 1;
+    gwn_status s = check_items(B, items, n_items, &leaves);
+    if (s != GWN_OK) return s;
+    std::lock_guard<std::mutex> lk(B->mu);
+    DeviceSwitch dsw(B->device);
+    s = ensure_workspaces(B, leaves);
     if (s != GWN_OK) return s;
     cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
-    if (!B->exec || !same_items(B->key, items, n_items)) {
-        drop_graph(B);
-        // largest item first, each to the least loaded stream
-        std::vector<size_t> order(n_items);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return items[a].n > items[b].n; });
-        const size_t ns = B->streams.size();
-        std::vector<double> load(ns, 0.0);
-        std::vector<std::vector<size_t>> plan(ns);
-        for (size_t i : order) {
-            size_t k = std::min_element(load.begin(), load.end()) - load.begin();
-            plan[k].push_back(i);
-            load[k] += (double)items[i].n + 65536.0;  // fixed cost per item
-        }
-        cudaStream_t cap = B->streams[0];
-        BATCH_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        gwn_status es = GWN_OK;
-        cudaError_t ce = cudaEventRecord(B->fork, cap);
-        for (size_t k = 1; k < ns && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(B->streams[k], B->fork, 0);
-        gwn_query_opts qo;
-        gwn_default_query_opts(&qo);
-        for (size_t k = 0; k < ns && ce == cudaSuccess && es == GWN_OK; ++k) {
-            for (size_t i : plan[k]) {
-                const gwn_query_item& it = items[i];
-                if (it.n == 0) continue;
-                es = gwn_enqueue_device(it.model, it.points, it.points_dtype, it.n, it.out_w, it.out_label,
-                                        it.out_status, qo, B->streams[k], B->ws[k]);
-                if (es != GWN_OK) break;
-            }
-            if (k > 0 && es == GWN_OK) {
-                ce = cudaEventRecord(B->done[k], B->streams[k]);
-                if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, B->done[k], 0);
-            }
-        }
-        cudaGraph_t g = nullptr;
-        cudaError_t ee = cudaStreamEndCapture(cap, &g);
-        if (es != GWN_OK) {
-            if (g) cudaGraphDestroy(g);
-            return es;
-        }
-        if (ce != cudaSuccess || ee != cudaSuccess || !g) {
-            if (g) cudaGraphDestroy(g);
-            return gwn_fail(GWN_ERR_CUDA, std::string("batch capture failed: ") +
-                                              cudaGetErrorString(ce != cudaSuccess ? ce : ee));
-        }
-        cudaGraphExec_t ex = nullptr;
-        ce = cudaGraphInstantiate(&ex, g, 0);
-        if (ce != cudaSuccess) {
-            cudaGraphDestroy(g);
-            return gwn_fail(GWN_ERR_CUDA, std::string("batch graph instantiation failed: ") + cudaGetErrorString(ce));
-        }
-        B->graph = g;
-        B->exec = ex;
-        B->key.assign(items, items + n_items);
-        B->captures += 1;
+    if (!B->exec || B->key_host || !same_items(B->key, items, n_items)) {
+        s = capture_plan(B, items, items, nullptr, n_items);
+        if (s != GWN_OK) return s;
     }
     // launches on different caller streams would share the workspaces: order
     // each after the previous one
@@ -211,12 +329,54 @@ gwn_status gwn_query_batch(gwn_batch B, const gwn_query_item* items, size_t n_it
     return GWN_OK;
 }
 
+gwn_status gwn_query_batch_host(gwn_batch B, const gwn_query_item* items, size_t n_items, void* stream) {
+    if (!B) return gwn_fail(GWN_ERR_INVALID_ARG, "batch is NULL");
+    if (n_items == 0) return GWN_OK;
+    if (!items) return gwn_fail(GWN_ERR_INVALID_ARG, "items is NULL");
+    int leaves = 1;
+    gwn_status s = check_items(B, items, n_items, &leaves);
+    if (s != GWN_OK) return s;
+    std::lock_guard<std::mutex> lk(B->mu);
+    DeviceSwitch dsw(B->device);
+    s = ensure_workspaces(B, leaves);
+    if (s != GWN_OK) return s;
+    std::vector<gwn_query_item> dev;
+    s = stage_items(B, items, n_items, &dev);
+    if (s != GWN_OK) return s;
+    cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+    bool locked = true;
+    for (size_t i = 0; i < n_items && locked; ++i)
+        locked = page_locked(items[i].points) && page_locked(items[i].out_w) && page_locked(items[i].out_label) &&
+                 page_locked(items[i].out_status);
+    if (B->last_recorded) BATCH_CUDA_TRY(cudaStreamWaitEvent(caller, B->last, 0));
+    if (locked) {
+        if (!B->exec || !B->key_host || !same_items(B->key, items, n_items)) {
+            s = capture_plan(B, items, dev.data(), items, n_items);
+            if (s != GWN_OK) return s;
+        }
+        BATCH_CUDA_TRY(cudaGraphLaunch(B->exec, caller));
+        B->launches += 1;
+    } else {
+        // pageable buffers: the same copies and kernels, issued directly
+        BATCH_CUDA_TRY(cudaEventRecord(B->fork, caller));
+        BATCH_CUDA_TRY(cudaStreamWaitEvent(B->streams[0], B->fork, 0));
+        s = issue_plan(B, dev.data(), items, n_items);
+        if (s != GWN_OK) return s;
+        BATCH_CUDA_TRY(cudaEventRecord(B->done[0], B->streams[0]));
+        BATCH_CUDA_TRY(cudaStreamWaitEvent(caller, B->done[0], 0));
+    }
+    BATCH_CUDA_TRY(cudaEventRecord(B->last, caller));
+    B->last_recorded = true;
+    BATCH_CUDA_TRY(cudaStreamSynchronize(caller));
+    return GWN_OK;
+}
+
 gwn_status gwn_batch_info(gwn_batch B, int64_t* graph_launches, int64_t* captures, int64_t* workspace_bytes) {
     if (!B) return gwn_fail(GWN_ERR_INVALID_ARG, "batch is NULL");
     std::lock_guard<std::mutex> lk(B->mu);
     if (graph_launches) *graph_launches = B->launches;
     if (captures) *captures = B->captures;
-    if (workspace_bytes) *workspace_bytes = (int64_t)(B->ws_bytes * B->streams.size());
+    if (workspace_bytes) *workspace_bytes = (int64_t)(B->ws_bytes * B->streams.size() + B->stage_bytes);
     return GWN_OK;
 }
 
@@ -229,6 +389,7 @@ gwn_status gwn_batch_release(gwn_batch B) {
         drop_graph(B);
         for (void* p : B->ws_mem)
             if (p) cudaFree(p);
+        if (B->stage) cudaFree(B->stage);
         for (cudaEvent_t e : B->done)
             if (e) cudaEventDestroy(e);
         if (B->fork) cudaEventDestroy(B->fork);

@@ -135,3 +135,26 @@ def test_autotuned_beta_2d(loops, oracle_lib):
     w_ref, fl = oracle_lib.gwn2d(curves, q[idx[:1500]])
     ok = np.isfinite(w_ref)
     assert np.max(np.abs(w[ok] - w_ref[ok])) <= 1e-4
+
+
+def test_loops_full_grid_against_exact_reference(loops, oracle_lib):
+    """Every query of the 1024^2 grid: the autotuned FP32 + repair traversal
+    against the exact GPU direct sum (itself held to the oracle on a seeded
+    sample here): max |dGWN| <= 1e-4 and identical labels away from
+    half-integers."""
+    from paper_2605_19200_gb300 import accuracy
+    curves, q, idx = loops
+    pts = torch.from_numpy(q).float().cuda()
+    m = gwn.gwn_build_2d(curves, beta=0.0, tolerance=1e-4)
+    w, lab, st = m.query(pts)
+    ref = accuracy.build_reference(curves, 2)
+    wr, lr, sr = accuracy.reference_values(ref, pts)
+    wr = wr.cpu().numpy()
+    sub = idx[:1500]
+    w_o, fl = oracle_lib.gwn2d(curves, q[sub])
+    ok = np.isfinite(w_o)
+    assert np.max(np.abs(wr[sub][ok] - w_o[ok])) <= 2e-6   # the reference itself
+    s = accuracy.compare(w.cpu().numpy(), lab.cpu().numpy(), wr)
+    assert s["checked"] == q.shape[0]
+    assert s["max_abs_dgwn"] <= 1e-4, s
+    assert s["label_mismatches"] == 0, s

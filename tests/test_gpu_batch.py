@@ -67,8 +67,46 @@ def test_batch_rejects_bad_items(items):
     b = gwn.Batch(n_streams=2)
     patches, _ = configs.cad_3d(35, 60, 0)
     host_only = gwn.gwn_build_3d(patches, beta=6.0, device=-2)
-    with pytest.raises(gwn.GwnError):
+    with pytest.raises((gwn.GwnError, TypeError)):
         b.query([host_only], [points[0]], [_outs(points[0].shape[0])])
     with pytest.raises(TypeError):
         b.query([models[0]], [points[0].to(torch.int32)], [_outs(points[0].shape[0])])
+    b.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_batch_host_buffers_match_device_batch(items, pinned):
+    """gwn_query_batch_host (points and outputs in host memory, copies made by
+    the library on the items' streams) gives the device batch's results; with
+    page-locked buffers the copies are captured in the graph and replayed."""
+    models, points = items
+    b = gwn.Batch(n_streams=3)
+    dev_outs = [_outs(p.shape[0]) for p in points]
+    b.query(models, points, dev_outs)
+    torch.cuda.synchronize()
+    ref = [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy()) for o in dev_outs]
+    if pinned:
+        hp = [p.cpu().pin_memory() for p in points]
+        mk = lambda n, dt: torch.empty(n, dtype=dt).pin_memory()
+        hout = [(mk(p.shape[0], torch.float64), mk(p.shape[0], torch.int32), mk(p.shape[0], torch.int32))
+                for p in points]
+    else:
+        hp = [p.cpu().numpy() for p in points]
+        hout = [(np.empty(p.shape[0]), np.empty(p.shape[0], np.int32), np.empty(p.shape[0], np.int32))
+                for p in points]
+    caps0 = b.info()["captures"]
+    for rep in range(2):
+        for o in hout:
+            o[0][:] = float("nan")
+        b.query_host(models, hp, hout)
+        for (w, lab, st), (wr, lr, sr) in zip(hout, ref):
+            w, lab = np.asarray(w), np.asarray(lab)
+            np.testing.assert_allclose(w, wr, rtol=0, atol=1e-5)
+            assert np.array_equal(lab, lr)
+    caps = b.info()["captures"] - caps0
+    assert caps == (1 if pinned else 0)
+    # the device batch still works after host calls (captured again)
+    b.query(models, points, dev_outs)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(dev_outs[0][0].cpu().numpy(), ref[0][0], rtol=0, atol=1e-5)
     b.close()

@@ -45,6 +45,7 @@ struct HostModel {
     std::vector<Curve3Info> c3;
     std::vector<float4> c3pts;
     std::vector<double> c3pts64;
+    std::vector<float4> c3n;       // kC3NodeVec per boundary curve
     std::vector<float4> c2;
     std::vector<double> c2_64;
     std::vector<float> c2mult;

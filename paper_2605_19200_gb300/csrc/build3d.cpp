@@ -498,6 +498,95 @@ void gauss_legendre01(int n, std::vector<double>* x, std::vector<double>* w) {
     }
 }
 
+// homogeneous point and derivative of a degree-D Bezier curve (D + 1 points of
+// 4 doubles in X) at t, by de Casteljau: the two points of the last-but-one
+// level give the derivative D (b1 - b0) and the point (1 - t) b0 + t b1
+void bez4_eval(const std::vector<double>& X, int D, double t, double P[4], double dP[4]) {
+    double b[kMaxC3Deg + 1][4];
+    for (int i = 0; i <= D; ++i)
+        for (int c = 0; c < 4; ++c) b[i][c] = X[(size_t)i * 4 + c];
+    for (int r = 1; r < D; ++r)
+        for (int i = 0; i <= D - r; ++i)
+            for (int c = 0; c < 4; ++c) b[i][c] = (1 - t) * b[i][c] + t * b[i + 1][c];
+    for (int c = 0; c < 4; ++c) {
+        dP[c] = D * (b[1][c] - b[0][c]);
+        P[c] = (1 - t) * b[0][c] + t * b[1][c];
+    }
+}
+
+// Panel level from which the 4-point Gauss-Legendre rule of the FP32 line
+// integral resolves the curve's own rational parametrisation.  The integrand
+// carries the tangent x'(t) = (X' W - X W') / W^2, whose poles (the complex
+// zeros of the weight W(t)) bound the rule's convergence: its error on a panel
+// falls like rho^-8, rho the Bernstein-ellipse parameter of the nearest pole.
+// On every panel of the returned level the rule must integrate x' itself --
+// whose exact integral is the chord x(b) - x(a) -- to 1e-6 of the panel's arc
+// length.  A quarter circle (weights 1, 1/sqrt 2, 1) composed with a bicubic
+// net has its poles at t = 1/2 +- 1.21 i: rho ~ 5 on [0, 1], ~ 10 on its halves.
+int curve_min_level(const std::vector<double>& X, int D, const std::vector<double>& x4, const std::vector<double>& w4) {
+    auto point = [&](double t, double x[3], double dx[3]) {
+        double P[4], dP[4];
+        bez4_eval(X, D, t, P, dP);
+        for (int c = 0; c < 3; ++c) {
+            x[c] = P[c] / P[3];
+            dx[c] = (dP[c] - x[c] * dP[3]) / P[3];
+        }
+    };
+    for (int L = 0; L < kMaxMinLevel; ++L) {
+        const int np = 1 << L;
+        const double h = 1.0 / np;
+        bool ok = true;
+        for (int p = 0; p < np && ok; ++p) {
+            double a[3], b[3], d[3], I[3] = {0, 0, 0}, arc = 0;
+            point(h * p, a, d);
+            point(h * (p + 1), b, d);
+            for (size_t k = 0; k < x4.size(); ++k) {
+                double x[3];
+                point(h * (p + x4[k]), x, d);
+                for (int c = 0; c < 3; ++c) I[c] += h * w4[k] * d[c];
+                arc += h * w4[k] * std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            }
+            const double e = std::sqrt((I[0] - (b[0] - a[0])) * (I[0] - (b[0] - a[0])) +
+                                       (I[1] - (b[1] - a[1])) * (I[1] - (b[1] - a[1])) +
+                                       (I[2] - (b[2] - a[2])) * (I[2] - (b[2] - a[2])));
+            ok = e <= 1e-6 * arc;
+        }
+        if (ok) return L;
+    }
+    return kMaxMinLevel;
+}
+
+// the node table of one boundary curve (Curve3Info / kC3NodeVec in
+// gwn_internal.h): positions relative to the leaf centre and derivatives at
+// the 4 Gauss-Legendre nodes of the level-0 panel and of the two level-1
+// panels, and each panel's length estimate (chords between the nodes x the
+// FP32 rule's span factor 1.17, as the kernels compute it)
+void node_table(const std::vector<double>& X, int D, const float cen[3], float mult, const std::vector<double>& x4,
+                float4 out[kC3NodeVec]) {
+    const double a0[3] = {0.0, 0.0, 0.5}, hh[3] = {1.0, 0.5, 0.5};
+    float len[3];
+    for (int p = 0; p < 3; ++p) {
+        float f[24];
+        double prev[3] = {0, 0, 0}, L = 0;
+        for (int k = 0; k < 4; ++k) {
+            double P[4], dP[4];
+            bez4_eval(X, D, a0[p] + hh[p] * x4[k], P, dP);
+            double x[3];
+            for (int c = 0; c < 3; ++c) {
+                x[c] = P[c] / P[3];
+                f[6 * k + c] = (float)(x[c] - (double)cen[c]);
+                f[6 * k + 3 + c] = (float)((dP[c] - x[c] * dP[3]) / P[3]);
+            }
+            if (k > 0) L += std::sqrt((x[0] - prev[0]) * (x[0] - prev[0]) + (x[1] - prev[1]) * (x[1] - prev[1]) +
+                                      (x[2] - prev[2]) * (x[2] - prev[2]));
+            for (int c = 0; c < 3; ++c) prev[c] = x[c];
+        }
+        len[p] = (float)(1.17 * L);
+        for (int v = 0; v < 6; ++v) out[1 + 6 * p + v] = float4{f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]};
+    }
+    out[0] = float4{len[0], len[1], len[2], mult};
+}
+
 // compose a local (u, v) piece with the bicubic net: 4D rational Bezier of degree 6 deg
 void compose(const TP& p, const Net& N, std::vector<double>* X) {
     int d = p.deg;
@@ -788,6 +877,8 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
     out->net3.resize((size_t)nl * kNet3Vec);
     out->net3_64.resize((size_t)nl * 64);
     std::vector<double> X;
+    std::vector<double> g4x, g4w;  // the FP32 rule: node tables and minimum levels
+    gauss_legendre01(4, &g4x, &g4w);
     for (int i = 0; i < nl; ++i) {
         const Leaf& L = leaves[perm[i]];
         out->leaf_prim[i] = L.prim;
@@ -821,8 +912,13 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
             ci.ctrl_off = (int32_t)out->c3pts.size();
             ci.deg = D;
             ci.mult = (float)L.mult[b];
-            ci.pad = 0.f;
+            ci.min_level = curve_min_level(X, D, g4x, g4w);
             out->c3.push_back(ci);
+            {
+                float4 tab[kC3NodeVec];
+                node_table(X, D, cen, ci.mult, g4x, tab);
+                out->c3n.insert(out->c3n.end(), tab, tab + kC3NodeVec);
+            }
             // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i),
             // then the same 2 D + 1 points of the reversed curve (evaluation for t > 1/2);
             // float copies relative to the leaf centre, double copies absolute

@@ -196,6 +196,7 @@ gwn_status upload_model(gwn_model_s* m) {
     UP(c3, c3);
     UP(c3pts, c3pts);
     UP(c3pts64, c3pts64);
+    UP(c3n, c3n);
     UP(c2, c2);
     UP(c2_64, c2_64);
     UP(c2mult, c2mult);
@@ -538,8 +539,13 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
                 k_scan<<<1, 1024, 0, st>>>(ws.hist, m->host.n_leaves);
                 k_pair_scatter<<<pb, 256, 0, st>>>(ws.pair_cap, ws.counters, ws.pairs, ws.key, ws.hist, ws.pairs2);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[2], st));
-                k_pair_eval<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters, ws.pairs2,
-                                                               ws.wacc, ws.st, ws.pairs64, ni, p.work);
+                // far pairs from the node tables; the rest, in leaf order, to the full
+                // evaluator (ws.pairs is free again once the sorted copy exists)
+                k_pair_fast<<<(unsigned)(sms * 16), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters,
+                                                                ws.pairs2, ws.wacc, ws.st, ws.pairs, p.work);
+                k_pair_eval<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters + 8,
+                                                               ws.counters, ws.pairs, ws.wacc, ws.st, ws.pairs64, ni,
+                                                               p.work);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[3], st));
                 if (round < 2) k_next_round<<<1, 32, 0, st>>>(ws);
             }
@@ -735,6 +741,7 @@ static gwn_status autotune(gwn_model_s* m) {
             }
             double cost = 10.0 * (wk[kWorkNodes] + wk[kWorkLeafTests]) + 72.0 * wk[kWorkFar] +
                           28.0 * wk[kWorkGlDeg] + 70.0 * wk[kWorkGlNodes] + 2000.0 * wk[kWorkHits] +
+                          kFastNodeFlops * wk[kWorkFastNodes] +
                           (d == 2 ? 60.0 * wk[kWorkLeaves] : 30.0 * wk[kWorkLeaves]);
             if (std::getenv("GWN_AUTOTUNE_VERBOSE"))
                 std::fprintf(stderr, "[gwn autotune] leaves=%d beta=%.1f beta_leaf=%.1f max|dGWN|=%.3g flops/pt=%.3g\n",
@@ -1014,7 +1021,9 @@ gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
     out[0] = (int64_t)(c[0] + c[7]);  // pairs over all rounds
     out[2] = (int64_t)c[2];           // near-band (FP64) pairs over all rounds
     out[3] = (int64_t)(c[6] + c[3]);  // points whose pairs overflowed in any round
-    for (int k = 0; k < kWorkCount; ++k) out[4 + k] = (int64_t)wk[k];
+    for (int k = 0; k < 8; ++k) out[4 + k] = (int64_t)wk[k];
+    out[14] = (int64_t)(c[8] + c[9]);  // pairs the full evaluator took (the rest came from the node tables)
+    out[15] = (int64_t)wk[kWorkFastNodes];
     if (m->profiled) {
         double a = 0, b = 0;
         for (int ch = 0; ch < m->prof_chunks; ++ch) {
@@ -1089,7 +1098,7 @@ gwn_status gwn_model_tree(gwn_model m, int32_t* child, double* x0, double* r, do
 
 namespace {
 constexpr char kModelMagic[8] = {'G', 'W', 'N', 'M', 'O', 'D', 'E', 'L'};
-constexpr uint32_t kModelVersion = 1;
+constexpr uint32_t kModelVersion = 2;
 
 template <typename V>
 bool write_vec(FILE* f, const std::vector<V>& v) {
@@ -1143,11 +1152,12 @@ bool host_model_consistent(const HostModel& H, int dim) {
         if (parents[k] != 1 && !(ni == 0 && k == 0)) return false;
     if (dim == 2) return H.leaf2.size() == nl * kLeaf2Vec && H.leaf2_64.size() == nl * kLeaf2F64;
     if (H.leaf3.size() != nl || H.net3.size() != nl * kNet3Vec || H.net3_64.size() != nl * 64 ||
-        H.c3pts64.size() != H.c3pts.size() * 4 || H.c2.size() != H.c2mult.size() * kC2Vec ||
+        H.c3pts64.size() != H.c3pts.size() * 4 || H.c3n.size() != H.c3.size() * kC3NodeVec ||
+        H.c2.size() != H.c2mult.size() * kC2Vec ||
         H.c2_64.size() != H.c2mult.size() * 12)
         return false;
     for (const Curve3Info& c : H.c3)
-        if (c.deg < 1 || c.deg > kMaxC3Deg || c.ctrl_off < 0 ||
+        if (c.deg < 1 || c.deg > kMaxC3Deg || c.ctrl_off < 0 || c.min_level < 0 || c.min_level > kMaxMinLevel ||
             (size_t)c.ctrl_off + 2 * (2 * (size_t)c.deg + 1) > H.c3pts.size())
             return false;
     for (const Leaf3Info& I : H.leaf3)
@@ -1163,7 +1173,7 @@ bool each_array(HostModel& H, F f) {
     return f(H.child) && f(H.hdr) && f(H.mom) && f(H.hdr64) && f(H.mom64) && f(H.lhdr) && f(H.lmom) &&
            f(H.lhdr64) && f(H.lmom64) && f(H.x0) && f(H.r) && f(H.mom_c) && f(H.leaf_prim) && f(H.leaf_param) &&
            f(H.leaf2) && f(H.leaf2_64) && f(H.leaf3) && f(H.net3) && f(H.net3_64) && f(H.c3) && f(H.c3pts) &&
-           f(H.c3pts64) && f(H.c2) && f(H.c2_64) && f(H.c2mult);
+           f(H.c3pts64) && f(H.c3n) && f(H.c2) && f(H.c2_64) && f(H.c2mult);
 }
 }  // namespace
 

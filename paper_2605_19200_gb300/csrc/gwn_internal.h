@@ -67,14 +67,35 @@ struct Leaf3Info {
 // their binomial coefficients C(D, i) c_i, followed by the D derivative points
 // C(D-1, i) (c_{i+1} - c_i), then the same 2 D + 1 points of the reversed
 // curve (evaluation for t > 1/2 reads them in forward order), and counted `mult`
-// times (winding multiplicity of a clipped rectangle edge).
+// times (winding multiplicity of a clipped rectangle edge).  min_level: the
+// FP32 line integral starts with 2^min_level panels, the level at which the
+// 4-point rule resolves the curve's own rational parametrisation (the complex
+// zeros of its weight polynomial; a quarter circle needs level 1).
 constexpr int kMaxC3Deg = 18;
+constexpr int kMaxMinLevel = 8;
 struct Curve3Info {
     int32_t ctrl_off;
     int32_t deg;
     float mult;
-    float pad;
+    int32_t min_level;
 };
+
+// Query-independent node table of one boundary curve (same index as its
+// Curve3Info), kC3NodeVec float4:
+//   [0]       (len0, len1a, len1b, mult): the length estimate of the level-0
+//             panel and of the two level-1 panels (sum of the chords between
+//             the 4 Gauss-Legendre nodes x the rule's span factor), and mult
+//   [1..6]    level-0 panel: 4 nodes x (x, y, z, dx/dt, dy/dt, dz/dt)
+//   [7..12]   level-1 panel [0, 1/2], same layout
+//   [13..18]  level-1 panel [1/2, 1]
+// with positions relative to the leaf centre.  A far (point, leaf) pair whose
+// panels stop at level 0 or 1 evaluates the line integral from this table
+// alone (leaf3_fast32): no curve evaluation per query.
+constexpr int kC3NodeVec = 19;
+// FP32 flops of one node read from a table (fast_panel in kernels3d.cuh): 3
+// subtractions and 31 multiply/add operations, plus a square root and a
+// reciprocal on the special-function unit
+constexpr double kFastNodeFlops = 34.0;
 
 // 2D boundary curve in local (u, v): rational cubic, 4 homogeneous points.
 constexpr int kC2Vec = 3;      // float4 per 2D local curve: (h0 h1 h2 h3) as 12 floats, multiplicity kept in Curve2Mult
@@ -106,6 +127,7 @@ struct DevTree {
     const Curve3Info* c3;
     const float4* c3pts;
     const double* c3pts64;     // 4 per point
+    const float4* c3n;         // kC3NodeVec per boundary curve
     const float4* c2;          // kC2Vec per local curve
     const double* c2_64;       // 12 per local curve
     const float* c2mult;
@@ -124,7 +146,8 @@ enum {
     kWorkGlDeg = 5,      // sum over those nodes of the curve degree D
     kWorkHits = 6,       // foot-point searches (3D near leaves)
     kWorkChords = 7,     // chord angles (2D leaf pieces)
-    kWorkCount = 8
+    kWorkFastNodes = 8,  // Gauss-Legendre nodes read from the node tables (leaf3_fast32)
+    kWorkCount = 9
 };
 
 struct WorkLocal {
@@ -160,7 +183,8 @@ struct Workspace {
     int2* pairs2;     // pair capacity (sorted)
     int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
                       // [5] overflowed points of the current round (list input), [6] total overflow,
-                      // [7] pairs of finished rounds
+                      // [7] pairs of finished rounds, [8] pairs left to the full evaluator this round,
+                      // [9] the same over finished rounds
     int* olist;       // n: points whose pairs did not fit (rounds alternate with olist2)
     int* olist2;      // n
     unsigned long long* work;  // kWorkCount counters

@@ -300,10 +300,15 @@ GWN_HD T panel_subtree(const G& g, int D, const T q[3], const T s[3], int level0
     }
 }
 
+// the whole curve, starting from the 2^min_level panels of level min_level
 template <typename T, typename G>
 GWN_HD T curve_line_integral(const G& g, int D, const T q[3], const T s[3], int maxlevel, T ratio, bool& deep,
-                             WorkLocal* wl = nullptr) {
-    return panel_subtree<T>(g, D, q, s, 0, 0u, maxlevel, ratio, deep, wl);
+                             WorkLocal* wl = nullptr, int min_level = 0) {
+    if (min_level <= 0) return panel_subtree<T>(g, D, q, s, 0, 0u, maxlevel, ratio, deep, wl);
+    T acc = 0;
+    for (unsigned idx = 0; idx < (1u << min_level); ++idx)
+        acc += panel_subtree<T>(g, D, q, s, min_level, idx, maxlevel, ratio, deep, wl);
+    return acc;
 }
 
 
@@ -538,7 +543,10 @@ GWN_HD bool leaf3_core(const DevTree& t, const Leaf3Info& I, const G& g, const T
         G gc = g;
         if (sizeof(T) == 4) gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts + ci.ctrl_off);
         else gc.pts = reinterpret_cast<decltype(gc.pts)>(t.c3pts64 + (size_t)ci.ctrl_off * 4);
-        acc += (T)ci.mult * curve_line_integral<T>(gc, ci.deg, q, s, maxlevel, ratio, deep, wl);
+        // the 4-point FP32 rule starts at the curve's own minimum level; the 8-point
+        // FP64 rule resolves the parametrisation from level 0
+        acc += (T)ci.mult * curve_line_integral<T>(gc, ci.deg, q, s, maxlevel, ratio, deep, wl,
+                                                   sizeof(T) == 4 ? ci.min_level : 0);
     }
     if (deep) return false;
     *out = acc * T(0.07957747154594767) - hits;  // 1 / (4 pi)
@@ -555,13 +563,92 @@ GWN_HD inline double leaf3_eval64(const DevTree& t, int li, double qx, double qy
     return w;
 }
 
-// FP32 evaluation only; false if the leaf needs the FP64 near band
+// One panel of 4 Gauss-Legendre nodes read from a node table (6 float4: x, y,
+// z, dx/dt, dy/dt, dz/dt per node): the weighted sum of the string potential's
+// integrand A_s(x - q) . x' and the minimum over the nodes of
+// min(|r|^2, 2 |r| (|r| + s.r)), the distance measure of the panel test.
+// Per node: 3 subtractions, 12 multiply-adds, a square root and a reciprocal.
+GWN_HD inline void fast_panel(const float4* P, const float q[3], const float s[3], float& psum, float& dmin2) {
+    float f[24];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+        const float4 a = GWN_LDG(P + v);
+        f[4 * v] = a.x; f[4 * v + 1] = a.y; f[4 * v + 2] = a.z; f[4 * v + 3] = a.w;
+    }
+    psum = 0.f;
+    dmin2 = 1e30f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float* n = f + 6 * k;
+        const float r0 = n[0] - q[0], r1 = n[1] - q[1], r2 = n[2] - q[2];
+        const float rr = r0 * r0 + r1 * r1 + r2 * r2;
+        const float rn = Num<float>::sqrt_fast(rr);
+        const float sr = s[0] * r0 + s[1] * r1 + s[2] * r2;
+        const float c0 = s[1] * r2 - s[2] * r1, c1 = s[2] * r0 - s[0] * r2, c2 = s[0] * r1 - s[1] * r0;
+        const float den = rn * (rn + sr);
+        psum += GWN_GLWF(k) * (c0 * n[3] + c1 * n[4] + c2 * n[5]) * Num<float>::rcp_fast(den);
+        dmin2 = fminf(dmin2, fminf(rr, 2.f * den));
+    }
+}
+
+// FP32 exact leaf from the node tables, for a point outside the sphere of
+// radius 1.1 x the leaf's half diagonal (q relative to the leaf centre, d2 =
+// |q|^2): the string points from q away from the leaf, so there is no crossing
+// to count, and every panel that the adaptive rule of leaf3_core would stop at
+// level 0 or 1 is read from the table.  Same rule, ratio and node positions as
+// leaf3_core<float> (the table's positions are rounded once from FP64).
+// Returns false if some curve needs a panel below level 1 (or starts below
+// it); the caller then evaluates the pair with leaf3_core.
+GWN_HD inline bool leaf3_fast32(const DevTree& t, const Leaf3Info& I, const float q[3], float d2, float* out,
+                                WorkLocal* wl = nullptr) {
+    const float l = Num<float>::rsqrt_(d2);
+    const float s[3] = {-q[0] * l, -q[1] * l, -q[2] * l};
+    const float ratio2 = kRatio32 * kRatio32;
+    float acc = 0.f;
+    int nodes = 0;
+    for (int c = 0; c < I.c3_cnt; ++c) {
+        const float4* H = t.c3n + (size_t)(I.c3_off + c) * kC3NodeVec;
+        const float4 hd = GWN_LDG(H);  // len0, len1a, len1b, mult
+        const int ml = t.c3[I.c3_off + c].min_level;
+        if (ml > 1) return false;
+        float psum, dmin2;
+        if (ml == 0) {
+            fast_panel(H + 1, q, s, psum, dmin2);
+            nodes += 4;
+            if (hd.x * hd.x <= ratio2 * dmin2) {
+                acc += hd.w * psum;
+                continue;
+            }
+        }
+        float pa, da, pb, db;
+        fast_panel(H + 7, q, s, pa, da);
+        fast_panel(H + 13, q, s, pb, db);
+        nodes += 8;
+        if (hd.y * hd.y > ratio2 * da || hd.z * hd.z > ratio2 * db) return false;
+        acc += hd.w * 0.5f * (pa + pb);
+    }
+    if (wl) {
+        wl->v[kWorkLeaves] += 1;
+        wl->v[kWorkFastNodes] += (unsigned long long)nodes;
+    }
+    *out = acc * 0.07957747154594767f;  // 1 / (4 pi)
+    return true;
+}
+
+// FP32 evaluation only; false if the leaf needs the FP64 near band.  With
+// try_fast, a point outside the leaf's 1.1-radius sphere first tries the
+// node tables (leaf3_fast32).
 GWN_HD inline bool leaf3_try32(const DevTree& t, int li, float qx, float qy, float qz, float* w,
-                               WorkLocal* wl = nullptr) {
+                               WorkLocal* wl = nullptr, bool try_fast = true) {
     Leaf3Info I = t.leaf3[li];
-    Geo32 g{t.net3 + (size_t)li * kNet3Vec, nullptr};
     float q[3] = {qx - I.cen[0], qy - I.cen[1], qz - I.cen[2]};
     *w = 0.f;
+    if (try_fast && t.c3n) {
+        const float d2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        const float rfar = 1.1f * I.rad;
+        if (d2 > rfar * rfar && leaf3_fast32(t, I, q, d2, w, wl)) return true;
+    }
+    Geo32 g{t.net3 + (size_t)li * kNet3Vec, nullptr};
     return leaf3_core<float>(t, I, g, q, w, kLevel32, kRatio32, wl);
 }
 

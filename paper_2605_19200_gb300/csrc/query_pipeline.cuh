@@ -14,8 +14,11 @@
 //  3. 3D only: the work list is counting-sorted by leaf, and one thread per pair
 //     evaluates the leaf in FP32 and adds it to the point's accumulator.
 //     Consecutive threads now share the same leaf, so a warp reads one set of
-//     boundary curves and runs mostly the same quadrature panels.  Pairs FP32
-//     cannot resolve go to the FP64 near band (one warp per pair).
+//     boundary curves.  Far pairs whose panels stop at level 0 or 1 (nearly
+//     all) read the curves' query-independent node tables (k_pair_fast); the
+//     rest take the full evaluation (k_pair_eval: foot-point search, adaptive
+//     panels from the Bernstein form).  Pairs FP32 cannot resolve go to the
+//     FP64 near band (one warp per pair).
 //  4. Finish: value, label and status per point; points whose value lies within
 //     the repair band of a half-integer, or that were flagged, are appended to
 //     the FP64 repair list (warp traversal + FP64 pairs, one warp per pair).
@@ -272,18 +275,70 @@ __global__ void k_pair_scatter(long long npair_cap, const int* counters, const i
     }
 }
 
-__global__ void __launch_bounds__(128, 5) k_pair_eval(DevTree t, const void* pts, int dtype, long long npair_cap,
-                                                   int* counters, const int2* pairs, float* wacc, uint32_t* st,
-                                                   int2* pairs64, int npair64_cap, unsigned long long* work) {
+// exact 3D leaves from the node tables, one thread per (point, leaf) pair in
+// leaf order (the 32 pairs of a warp mostly share one leaf, so its table is
+// read once for the warp): pairs whose point lies outside the leaf's
+// 1.1-radius sphere and whose panels stop at level 0 or 1 add their value
+// here (leaf3_fast32).  The others -- points near the leaf, whose string needs
+// the foot-point search, and curves that need deeper panels -- are appended in
+// order to `slow` (counter [8]) for k_pair_eval.  Every thread of a block runs
+// the same iterations, so a warp appends with a single atomic.
+__global__ void __launch_bounds__(128) k_pair_fast(DevTree t, const void* pts, int dtype, long long npair_cap,
+                                                   int* counters, const int2* pairs, float* wacc, const uint32_t* st,
+                                                   int2* slow, unsigned long long* work) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     WorkLocal wl = {};
-    long long np = min((long long)counters[0], npair_cap);
+    const long long np = min((long long)counters[0], npair_cap);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long k = base + threadIdx.x;
+        bool to_slow = false;
+        int2 pr = make_int2(0, 0);
+        if (k < np) {
+            pr = pairs[k];
+            if (!(st[pr.x] & kPairOverflow)) {  // overflowed points are recomputed by k_overflow3
+                float q[3];
+                load_point_f(pts, dtype, 3, pr.x, q);
+                const Leaf3Info I = t.leaf3[pr.y];
+                const float qr[3] = {q[0] - I.cen[0], q[1] - I.cen[1], q[2] - I.cen[2]};
+                const float d2 = qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2];
+                const float rfar = 1.1f * I.rad;
+                float v;
+                if (d2 > rfar * rfar && leaf3_fast32(t, I, qr, d2, &v, work ? &wl : nullptr))
+                    atomicAdd(&wacc[pr.x], v);
+                else
+                    to_slow = true;
+            }
+        }
+        const unsigned m = __ballot_sync(full, to_slow);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int slot0 = 0;
+            if (lane == leader) slot0 = atomicAdd(&counters[8], __popc(m));
+            slot0 = __shfl_sync(full, slot0, leader);
+            if (to_slow) slow[slot0 + __popc(m & ((1u << lane) - 1u))] = pr;
+        }
+    }
+    if (work) flush_work(wl, work);
+}
+
+// the pairs that k_pair_fast left (count *count): the full FP32 evaluation
+// (foot-point search, adaptive panels from the curves' Bernstein form); pairs
+// FP32 cannot resolve go to the FP64 near band
+__global__ void __launch_bounds__(128, 5) k_pair_eval(DevTree t, const void* pts, int dtype, long long npair_cap,
+                                                   const int* count, int* counters, const int2* pairs, float* wacc,
+                                                   uint32_t* st, int2* pairs64, int npair64_cap,
+                                                   unsigned long long* work) {
+    WorkLocal wl = {};
+    long long np = min((long long)*count, npair_cap);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
         int2 pr = pairs[k];
         if (st[pr.x] & kPairOverflow) continue;  // recomputed by k_overflow3
         float q[3];
         load_point_f(pts, dtype, 3, pr.x, q);
         float v;
-        if (leaf3_try32(t, pr.y, q[0], q[1], q[2], &v, work ? &wl : nullptr)) {
+        if (leaf3_try32(t, pr.y, q[0], q[1], q[2], &v, work ? &wl : nullptr, false)) {
             atomicAdd(&wacc[pr.x], v);
         } else {
             int slot = atomicAdd(&counters[2], 1);
@@ -463,8 +518,10 @@ __global__ void k_next_round(Workspace ws) {
         ws.counters[5] = ws.counters[3];
         ws.counters[6] += ws.counters[3];
         ws.counters[7] += ws.counters[0];  // pairs of the finished round
+        ws.counters[9] += ws.counters[8];  // of which the full evaluator took
         ws.counters[3] = 0;
         ws.counters[0] = 0;  // the near-band list (counters[2]) spans all rounds
+        ws.counters[8] = 0;
     }
 }
 

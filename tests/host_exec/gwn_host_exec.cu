@@ -75,6 +75,7 @@ DevTree host_tree(const HostModel& H, int leaf_far) {
     t.c3 = H.c3.data();
     t.c3pts = H.c3pts.data();
     t.c3pts64 = H.c3pts64.data();
+    t.c3n = H.c3n.empty() ? nullptr : H.c3n.data();
     t.c2 = H.c2.data();
     t.c2_64 = H.c2_64.data();
     t.c2mult = H.c2mult.data();
@@ -139,5 +140,35 @@ extern "C" int hx_query2(const gwn_curve2d* curves, size_t n, const gwn_build_op
             work[2] += (long long)wl.v[kWorkLeaves];
         }
     }
+    return t.n_leaves;
+}
+
+// Per (query, leaf) pair of a direct sum: the FP32 value from the node tables
+// (fast32, NaN where leaf3_fast32 declines: the point is near the leaf or a
+// curve needs panels below level 1), the full FP32 evaluation (full32, NaN
+// where it needs the FP64 near band) and the FP64 evaluation (exact64).
+// Arrays hold nq x n_leaves values.  Returns the number of leaves.
+extern "C" int hx_leaf_paths3(const gwn_patch3d* patches, size_t n, const gwn_build_opts* o, const double* q, int nq,
+                              double* fast32, double* full32, double* exact64, int max_leaves) {
+    init_tables();
+    HostModel H;
+    gwn_status code;
+    if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
+    const DevTree t = host_tree(H, 1);
+    if (t.n_leaves > max_leaves) return -2;
+    for (int i = 0; i < nq; ++i)
+        for (int l = 0; l < t.n_leaves; ++l) {
+            const size_t k = (size_t)i * t.n_leaves + l;
+            const Leaf3Info I = t.leaf3[l];
+            const float qf[3] = {(float)q[3 * i], (float)q[3 * i + 1], (float)q[3 * i + 2]};
+            const float qr[3] = {qf[0] - I.cen[0], qf[1] - I.cen[1], qf[2] - I.cen[2]};
+            const float d2 = qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2];
+            const float rfar = 1.1f * I.rad;
+            float v = 0.f;
+            fast32[k] = (d2 > rfar * rfar && leaf3_fast32(t, I, qr, d2, &v)) ? (double)v : NAN;
+            full32[k] = leaf3_try32(t, l, qf[0], qf[1], qf[2], &v, nullptr, false) ? (double)v : NAN;
+            uint32_t st = 0;
+            exact64[k] = leaf3_eval64(t, l, (double)qf[0], (double)qf[1], (double)qf[2], st);
+        }
     return t.n_leaves;
 }

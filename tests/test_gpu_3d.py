@@ -215,7 +215,7 @@ def test_sphere_full_set_against_exact_reference(sphere):
     wr, lr, sr = accuracy.reference_values(ref, pts)
     wr = wr.cpu().numpy()
     ok = np.isfinite(w_ref)
-    assert np.max(np.abs(wr[idx][ok] - w_ref[ok])) <= 2e-6   # the reference itself
+    assert np.max(np.abs(wr[idx][ok] - w_ref[ok])) <= 5e-6   # the reference itself
     s = accuracy.compare(w.cpu().numpy(), lab.cpu().numpy(), wr)
     assert s["checked"] == q.shape[0]
     assert s["max_abs_dgwn"] <= 1e-4, s

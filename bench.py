@@ -52,7 +52,6 @@ ACCURACY_SAMPLE = 65536  # seeded queries per model compared with the exact GPU 
 ACCURACY_SEED = 2026
 WORKLOAD_NAME = ("cad16: 16 models of trimmed bicubic rational patches (box/cylinder unions), "
                  "queries uniform in each model's box")
-PAIR_EVAL_DRAM_BYTES_PER_PAIR = 10.5  # ncu dram__bytes_read + dram__bytes_write of k_pair_eval per pair
 
 
 def patches_box(patches):
@@ -134,11 +133,16 @@ def flops_traversal(w):
     return 10 * (w["nodes"] + w["leaf_tests"]) + 72 * w["far"]
 
 
+FAST_NODE_FLOPS = 34    # a node read from a curve's node table: r, |r|, s.r, s x r, the integrand (+ 2 SFU ops)
+
+
 def flops_leaves(w):
-    # per Gauss-Legendre node of a degree-D boundary curve: 28 D + 70 (value and
-    # derivative by Horner's rule, string potential); per foot-point search 2000;
-    # per leaf evaluation set-up 30
-    return 28 * w["gl_deg"] + 70 * w["gl_nodes"] + 2000 * w["hits"] + 30 * w["leaves"]
+    # per Gauss-Legendre node of a degree-D boundary curve evaluated from its
+    # Bernstein form: 28 D + 70 (value and derivative by Horner's rule, string
+    # potential); per node read from a node table: 34; per foot-point search
+    # 2000; per leaf evaluation set-up 30
+    return (28 * w["gl_deg"] + 70 * w["gl_nodes"] + FAST_NODE_FLOPS * w["fast_nodes"] + 2000 * w["hits"] +
+            30 * w["leaves"])
 
 
 def fp32_peak_tflops(sm_mhz, sms):
@@ -428,40 +432,44 @@ def main():
                               "ms_per_step": ms, "queries_per_step": total_q}), flush=True)
         return
 
-    # kernel-level numbers (untimed passes): event timing of the traversal and
-    # exact-leaf kernels on the query stream, and the algorithmic work counters
-    trav_us, leaf_us, fl_trav, fl_leaf, repaired, pairs, near = 0.0, 0.0, 0.0, 0.0, 0, 0, 0
+    # kernel-level numbers (untimed passes): event timing of the traversal, the
+    # node-table and the full exact-leaf kernels on the query stream, and the
+    # algorithmic work counters
+    us = {"k_trav3": 0.0, "k_pair_fast": 0.0, "k_pair_eval": 0.0}
+    fl = {"k_trav3": 0.0, "k_pair_fast": 0.0, "k_pair_eval": 0.0}
+    repaired, pairs, near, full_pairs = 0, 0, 0, 0
+    work_tot = {"fast_nodes": 0, "gl_nodes": 0, "hits": 0, "nodes": 0, "far": 0}
     for m, p, o in zip(models, points, outs):
         m.query(p, out=o, stream=stream, profile=True)
         s = m.last_query_stats()
-        trav_us += s["trav_us"]
-        leaf_us += s["leaf_us"]
+        us["k_trav3"] += s["trav_us"]
+        us["k_pair_fast"] += s["fast_us"]
+        us["k_pair_eval"] += s["full_us"]
         m.query(p, out=o, stream=stream, count_work=True)
         w = m.last_query_stats()
-        fl_trav += flops_traversal(w)
-        fl_leaf += flops_leaves(w)
+        fl["k_trav3"] += flops_traversal(w)
+        fl["k_pair_fast"] += FAST_NODE_FLOPS * w["fast_nodes"]
+        fl["k_pair_eval"] += flops_leaves(w) - FAST_NODE_FLOPS * w["fast_nodes"]
         repaired += w["repaired"]
         pairs += w["pairs"]
         near += w["near_band"]
+        full_pairs += w["full_pairs"]
+        for k in ("fast_nodes", "gl_nodes", "hits", "nodes", "far"):
+            work_tot[k] += w[k]
     log("profiled and counted")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = fp32_peak_tflops(sm_mhz, sms)
-    dominant = "k_pair_eval" if leaf_us >= trav_us else "k_trav3"
-    d_us, d_fl = (leaf_us, fl_leaf) if dominant == "k_pair_eval" else (trav_us, fl_trav)
-    # per launch: algorithmic flops / event-timed duration (summed over the 16 launches of a step)
-    achieved = d_fl / (d_us * 1e-6) / 1e12
-    # DRAM bytes (read + written) per (query, leaf) pair of k_pair_eval, from one ncu capture of
-    # this kernel on a one-model case, scaled to the average launch of a step by its pairs
-    n_pair_launches = sum(3 * math.ceil(p.shape[0] / (1 << 19)) for p in points)
-    traffic = (PAIR_EVAL_DRAM_BYTES_PER_PAIR * pairs / n_pair_launches
-               if dominant == "k_pair_eval" and pairs > 0 else None)
+    dominant = max(us, key=us.get)
+    # per launch: algorithmic flops / event-timed duration (both summed over the
+    # step's launches of the kernel, first round of each chunk)
+    achieved = fl[dominant] / (us[dominant] * 1e-6) / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "traffic_note": "DRAM bytes per average k_pair_eval launch: 10.5 B per pair (ncu, one-model "
-                                "capture) x pairs of a step / launches of a step",
+                "frac": achieved / peak, "traffic": None,
+                "traffic_note": "ncu DRAM counters of the current kernels are in profiles/, not in this run",
                 "peak_note": f"FP32 FMA issue: {sms} SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median under load)",
-                "trav_ms_per_step": trav_us / 1e3, "leaf_ms_per_step": leaf_us / 1e3}
+                "ms_per_step": {k: v / 1e3 for k, v in us.items()},
+                "tflops": {k: (fl[k] / (us[k] * 1e-6) / 1e12 if us[k] > 0 else None) for k in us}}
 
     # e2e through the C ABI with host buffers: gwn_query_batch_host copies every
     # model's points in and its values and labels out (one cudaMemcpyAsync per
@@ -489,7 +497,7 @@ def main():
     _, e2e_value = aggregate_ranks(e2e_s * 1e3, total_q, world, dev)
     h2d = sum(p.numel() * p.element_size() for p in points)
     d2h = sum(p.shape[0] * (8 + 4) for p in points)
-    e2e_match = all(np.array_equal(ho[0].numpy(), o[0].cpu().numpy()) for ho, o in zip(host_out, outs))
+    e2e_diff = max(float(np.max(np.abs(ho[0].numpy() - o[0].cpu().numpy()))) for ho, o in zip(host_out, outs))
     hbatch.close()
 
     # plain GPU direct sum (every unsubdivided patch exact) on a sample of each
@@ -597,14 +605,20 @@ def main():
                               if batch is not None else "one gwn_query per model")},
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "gwn_query_batch_host (pinned host buffers, one graph launch)",
-                "steps": args.steps, "outputs_equal_device_run": bool(e2e_match)},
+                "steps": args.steps, "max_abs_diff_vs_device_run": e2e_diff},
         "roofline": roofline,
         "accuracy": acc,
         "direct_sum": {"value": direct_qps, "unit": "queries/s",
                        "sample": f"{DIRECT_SAMPLE} queries per model, FP32, per-query time extrapolated",
                        "speedup": value / direct_qps},
         "work": {"pairs_per_query": pairs / total_q, "near_band_pairs_per_query": near / total_q,
-                 "repaired_fraction": repaired / total_q},
+                 "repaired_fraction": repaired / total_q,
+                 "full_evaluator_pair_fraction": full_pairs / max(pairs, 1),
+                 "table_nodes_per_query": work_tot["fast_nodes"] / total_q,
+                 "bernstein_nodes_per_query": work_tot["gl_nodes"] / total_q,
+                 "foot_point_searches_per_query": work_tot["hits"] / total_q,
+                 "nodes_visited_per_query": work_tot["nodes"] / total_q,
+                 "taylor_terms_per_query": work_tot["far"] / total_q},
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
     }

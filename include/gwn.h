@@ -214,7 +214,7 @@ typedef struct {
 gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
 
 /* Work counters of the last gwn_query on this model (synchronises the
- * device).  out holds 16 int64:
+ * device).  out holds 20 int64:
  *   out[0] exact-leaf (point, leaf) pairs of the 3D traversal
  *   out[1] points re-evaluated in FP64 (repair)
  *   out[2] 3D leaf evaluations moved to the FP64 near band
@@ -223,7 +223,13 @@ gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
  *     evaluations, exact leaf evaluations, Gauss-Legendre nodes, sum of curve
  *     degrees over those nodes, foot-point searches, 2D chord angles
  *   out[12..13] with profile: traversal and exact-leaf kernel time in
- *     microseconds (CUDA events on the query's stream) */
+ *     microseconds (CUDA events on the query's stream)
+ *   out[14] exact-leaf pairs evaluated by the full evaluator (the others were
+ *     read from the boundary curves' node tables)
+ *   out[15] with count_work: Gauss-Legendre nodes read from the node tables
+ *   out[16..17] with profile: the exact-leaf time split into the node-table
+ *     kernel and the full evaluator (microseconds)
+ *   out[18..19] zero (reserved) */
 gwn_status gwn_last_query_stats(gwn_model model, int64_t* out);
 
 /* Copy per-leaf records to host memory for inspection (used by the tests).

@@ -216,10 +216,11 @@ class Model:
         return {f: (list(getattr(s, f)) if f in ("lo", "hi") else getattr(s, f)) for f, _ in s._fields_}
 
     def last_query_stats(self) -> dict:
-        out = np.zeros(16, dtype=np.int64)
+        out = np.zeros(20, dtype=np.int64)
         _check(lib().gwn_last_query_stats(self.handle, out.ctypes.data))
         names = ["pairs", "repaired", "near_band", "overflow", "nodes", "leaf_tests", "far", "leaves",
-                 "gl_nodes", "gl_deg", "hits", "chords", "trav_us", "leaf_us"]
+                 "gl_nodes", "gl_deg", "hits", "chords", "trav_us", "leaf_us", "full_pairs", "fast_nodes",
+                 "fast_us", "full_us"]
         return {k: int(out[i]) for i, k in enumerate(names)}
 
     def leaves(self):

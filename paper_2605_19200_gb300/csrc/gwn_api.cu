@@ -401,6 +401,7 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
 }
 
 constexpr size_t kChunk = (size_t)1 << 19;  // points per pass of the query pipeline
+constexpr int kQueryStats = 20;              // entries of gwn_last_query_stats
 
 // beta of the FP64 repair when the build leaves it automatic: the exact sum over
 // every leaf for small models, else the traversal at 3 beta, whose order-2
@@ -446,7 +447,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
     cudaEvent_t* ev = prof ? m->ev[pc] : nullptr;
     if (prof) {
         if (!ev[0])
-            for (int k = 0; k < 4; ++k) GWN_CUDA_TRY(cudaEventCreate(&ev[k]));
+            for (int k = 0; k < 5; ++k) GWN_CUDA_TRY(cudaEventCreate(&ev[k]));
         m->prof_chunks = pc + 1;
     }
     double beta = qo.beta > 0 ? qo.beta : m->opts.beta;
@@ -520,6 +521,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
             if (prof) {
                 GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
                 GWN_CUDA_TRY(cudaEventRecord(ev[2], st));
+                GWN_CUDA_TRY(cudaEventRecord(ev[4], st));
                 GWN_CUDA_TRY(cudaEventRecord(ev[3], st));
             }
         } else {
@@ -543,6 +545,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
                 // evaluator (ws.pairs is free again once the sorted copy exists)
                 k_pair_fast<<<(unsigned)(sms * 16), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters,
                                                                 ws.pairs2, ws.wacc, ws.st, ws.pairs, p.work);
+                if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[4], st));
                 k_pair_eval<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters + 8,
                                                                ws.counters, ws.pairs, ws.wacc, ws.st, ws.pairs64, ni,
                                                                p.work);
@@ -1016,7 +1019,7 @@ gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
         GWN_CUDA_TRY(cudaMemcpy(c, m->ws.acc, sizeof(c), cudaMemcpyDeviceToHost));
         GWN_CUDA_TRY(cudaMemcpy(wk, m->ws.work, sizeof(wk), cudaMemcpyDeviceToHost));
     }
-    for (int k = 0; k < 16; ++k) out[k] = 0;
+    for (int k = 0; k < kQueryStats; ++k) out[k] = 0;
     for (int k = 0; k < 4; ++k) out[k] = (int64_t)c[k];
     out[0] = (int64_t)(c[0] + c[7]);  // pairs over all rounds
     out[2] = (int64_t)c[2];           // near-band (FP64) pairs over all rounds
@@ -1025,17 +1028,21 @@ gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
     out[14] = (int64_t)(c[8] + c[9]);  // pairs the full evaluator took (the rest came from the node tables)
     out[15] = (int64_t)wk[kWorkFastNodes];
     if (m->profiled) {
-        double a = 0, b = 0;
+        double a = 0, b = 0, f = 0;
         for (int ch = 0; ch < m->prof_chunks; ++ch) {
-            float x = 0, y = 0;
+            float x = 0, y = 0, z = 0;
             GWN_CUDA_TRY(cudaEventSynchronize(m->ev[ch][3]));
             GWN_CUDA_TRY(cudaEventElapsedTime(&x, m->ev[ch][0], m->ev[ch][1]));
             GWN_CUDA_TRY(cudaEventElapsedTime(&y, m->ev[ch][2], m->ev[ch][3]));
+            GWN_CUDA_TRY(cudaEventElapsedTime(&z, m->ev[ch][2], m->ev[ch][4]));
             a += x;
             b += y;
+            f += z;
         }
         out[12] = (int64_t)(a * 1000.0);
         out[13] = (int64_t)(b * 1000.0);
+        out[16] = (int64_t)(f * 1000.0);
+        out[17] = (int64_t)((b - f) * 1000.0);
     }
     return GWN_OK;
 }

@@ -627,10 +627,7 @@ GWN_HD inline bool leaf3_fast32(const DevTree& t, const Leaf3Info& I, const floa
         if (hd.y * hd.y > ratio2 * da || hd.z * hd.z > ratio2 * db) return false;
         acc += hd.w * 0.5f * (pa + pb);
     }
-    if (wl) {
-        wl->v[kWorkLeaves] += 1;
-        wl->v[kWorkFastNodes] += (unsigned long long)nodes;
-    }
+    if (wl) wl->v[kWorkFastNodes] += (unsigned long long)nodes;  // kWorkLeaves counts the full evaluations
     *out = acc * 0.07957747154594767f;  // 1 / (4 pi)
     return true;
 }

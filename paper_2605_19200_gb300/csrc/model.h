@@ -30,7 +30,9 @@ struct gwn_model_s {
     size_t ws_n = 0;
     gwn::Workspace ws{};
     static constexpr int kMaxProfChunks = 32;
-    cudaEvent_t ev[kMaxProfChunks][4] = {};
+    // per chunk: before and after the traversal, before the table kernel,
+    // after the full evaluator, between the two (round 0 of each chunk)
+    cudaEvent_t ev[kMaxProfChunks][5] = {};
     int prof_chunks = 0;
     bool profiled = false;
     void* stage = nullptr;

@@ -194,8 +194,10 @@ def serving_leg(gwn, phase_s: float, log_fn):
 
     Phase 1 (saturation): the first requests of the trace, about phase_s seconds
     of work, are submitted at once; sustained throughput = points / time to
-    drain.  Phase 2 (open loop): Poisson arrivals at half the saturated request
-    rate for phase_s seconds; p50/p99 of submit -> results ready.
+    drain.  Phase 2 (open loop, a load sweep): Poisson arrivals at 0.25, 0.5,
+    0.75 and 0.9 of the saturated request rate, phase_s seconds each; p50/p99
+    of submit -> results ready, and the most requests whose device work
+    overlapped.
     """
     import threading as th
     from synth import configs
@@ -246,23 +248,27 @@ def serving_leg(gwn, phase_s: float, log_fn):
     st, wall = run(t_all[:k], m_all[:k], n_all[:k], open_loop=False)
     sat_qps = st["points_completed"] / wall
     sat_rps = k / wall
-    log_fn(f"serving: saturation {sat_qps:.3e} points/s, {sat_rps:.1f} req/s")
-    rate = 0.5 * sat_rps
-    t_o, m_o, n_o = configs.serve_trace(rate, phase_s, seed=configs.BASE_SEED + 7)
-    st2, wall2 = run(t_o, m_o, n_o, open_loop=True)
-    log_fn(f"serving: open loop {rate:.1f} req/s, p50 {st2['p50_ms']:.1f} ms, p99 {st2['p99_ms']:.1f} ms")
+    log_fn(f"serving: saturation {sat_qps:.3e} points/s, {sat_rps:.1f} req/s, "
+           f"max overlap on the GPU {st['max_gpu_overlap']}")
+    sweep = []
+    for i, load in enumerate((0.25, 0.5, 0.75, 0.9)):
+        rate = load * sat_rps
+        t_o, m_o, n_o = configs.serve_trace(rate, phase_s, seed=configs.BASE_SEED + 7 + i)
+        st2, wall2 = run(t_o, m_o, n_o, open_loop=True)
+        sweep.append({"load": load, "rate_req_s": rate, "duration_s": phase_s, "requests": int(st2["completed"]),
+                      "p50_ms": st2["p50_ms"], "p99_ms": st2["p99_ms"], "mean_ms": st2["mean_ms"],
+                      "points_per_s": st2["points_completed"] / wall2, "max_in_flight": int(st2["max_in_flight"]),
+                      "max_gpu_overlap": int(st2["max_gpu_overlap"])})
+        log_fn(f"serving: load {load} ({rate:.1f} req/s): p50 {st2['p50_ms']:.1f} ms, p99 {st2['p99_ms']:.1f} ms")
     for m in models:
         m.release()
     return {"metric": "serving latency, submit -> results ready", "unit": "ms",
             "models": "8 resident: 2 loops_2d (19,000 curves), 2 sphere_3d (384 patches), "
                       "4 cad_3d (1.5k-17k patches)",
             "sizes": "log-normal, median 16,384 points, sigma 1.5, clamped to [1000, 2e6]",
-            "saturation": {"requests": k, "points_per_s": sat_qps, "requests_per_s": sat_rps},
-            "open_loop": {"rate_req_s": rate, "load": 0.5, "duration_s": phase_s,
-                          "requests": int(st2["completed"]), "p50_ms": st2["p50_ms"],
-                          "p99_ms": st2["p99_ms"], "mean_ms": st2["mean_ms"],
-                          "points_per_s": st2["points_completed"] / wall2},
-            "slots": 4, "precision": "fp32 bulk + fp64 repair"}
+            "saturation": {"requests": k, "points_per_s": sat_qps, "requests_per_s": sat_rps,
+                           "max_gpu_overlap": int(st["max_gpu_overlap"])},
+            "load_sweep": sweep, "slots": 4, "precision": "fp32 bulk + fp64 repair"}
 
 
 def config_leg(config: int, steps: int, warmup: int) -> dict:
@@ -343,7 +349,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the single-model configurations 1-3")
     ap.add_argument("--streams", type=int, default=4,
                     help="streams of the batched query (one graph launch per step); 0 = one gwn_query per model")
-    ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving phase")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of each serving phase")
     ap.add_argument("--kernels-only", action="store_true",
                     help="timed steps only (no e2e, direct-sum or CPU legs); for profiler runs")
     ap.add_argument("--config", type=int, default=0, choices=[0, 1, 2, 3],

@@ -362,6 +362,9 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms;  /* submit -> results ready, over completed requests */
     double queries_per_s;            /* points completed / (last completion - first submit) */
     int64_t budget_used_bytes;
+    int64_t max_in_flight;           /* most slots occupied at once (admitted, not finished) */
+    int64_t max_gpu_overlap;         /* most completed requests whose device work windows (copy in .. copy
+                                        out, CUDA events on their slots' streams) overlapped in time */
 } gwn_server_stats;
 
 gwn_status gwn_serve_stats(gwn_server server, gwn_server_stats* stats);

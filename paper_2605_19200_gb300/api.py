@@ -75,7 +75,8 @@ class gwn_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("in_flight", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("points_completed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("queries_per_s", ctypes.c_double),
-                ("budget_used_bytes", ctypes.c_int64)]
+                ("budget_used_bytes", ctypes.c_int64), ("max_in_flight", ctypes.c_int64),
+                ("max_gpu_overlap", ctypes.c_int64)]
 
 
 class gwn_query_item(ctypes.Structure):

@@ -47,6 +47,7 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;  // timing: the current request's device work begins / ends
     void* ws_mem = nullptr;
     gwn::Workspace ws{};
     size_t ws_bytes = 0;
@@ -70,6 +71,11 @@ struct gwn_server_s {
     std::deque<std::shared_ptr<Request>> queue;
     std::map<uint64_t, std::shared_ptr<Request>> reqs;
     std::vector<double> latencies_ms;
+    // device windows of completed requests (ms since `ref`): evidence that the
+    // work of requests in different slots overlaps on the GPU
+    cudaEvent_t ref = nullptr;
+    std::vector<std::pair<double, double>> windows;
+    int64_t max_in_flight = 0;
     uint64_t next_id = 1;
     int64_t submitted = 0, completed = 0, points_done = 0;
     clk::time_point t_first{}, t_last{};
@@ -95,7 +101,8 @@ size_t request_dev_bytes(const gwn_server_s* s, const Request& r) {
 gwn_status ensure_slot(gwn_server_s* S, Slot& sl, size_t pin_bytes) {
     if (!sl.stream) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&sl.t0) != cudaSuccess || cudaEventCreate(&sl.t1) != cudaSuccess)
             return gwn_fail(GWN_ERR_CUDA, "serve: stream/event creation failed");
     }
     if (!sl.ws_mem) {
@@ -132,7 +139,8 @@ gwn_status launch(gwn_server_s* S, Slot& sl, Request& r) {
     double* dw = reinterpret_cast<double*>(sl.dev + ((pb + 255) & ~size_t(255)));
     int32_t* dl = reinterpret_cast<int32_t*>(dw + r.n);
     std::memcpy(sl.pin_in, r.points.data(), pb);
-    if (cudaMemcpyAsync(dpts, sl.pin_in, pb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+    if (cudaEventRecord(sl.t0, sl.stream) != cudaSuccess ||
+        cudaMemcpyAsync(dpts, sl.pin_in, pb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
         return gwn_fail(GWN_ERR_CUDA, "serve: copy in");
     gwn_query_opts qo;
     gwn_default_query_opts(&qo);
@@ -142,19 +150,25 @@ gwn_status launch(gwn_server_s* S, Slot& sl, Request& r) {
         cudaFreeAsync(sl.dev, sl.stream) != cudaSuccess)
         return gwn_fail(GWN_ERR_CUDA, "serve: copy out");
     sl.dev = nullptr;
-    if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return gwn_fail(GWN_ERR_CUDA, "serve: event");
+    if (cudaEventRecord(sl.t1, sl.stream) != cudaSuccess || cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
+        return gwn_fail(GWN_ERR_CUDA, "serve: event");
     return GWN_OK;
 }
 
 void finish(gwn_server_s* S, Slot& sl) {
     Request& r = *sl.cur;
+    float a = -1.f, b = -1.f;
     if (r.status == GWN_OK) {
         r.w.resize(r.n);
         r.label.resize(r.n);
         std::memcpy(r.w.data(), sl.pin_out, r.n * sizeof(double));
         std::memcpy(r.label.data(), reinterpret_cast<char*>(sl.pin_out) + r.n * sizeof(double), r.n * sizeof(int32_t));
+        if (S->ref && (cudaEventElapsedTime(&a, S->ref, sl.t0) != cudaSuccess ||
+                       cudaEventElapsedTime(&b, S->ref, sl.t1) != cudaSuccess))
+            a = b = -1.f;
     }
     std::lock_guard<std::mutex> lk(S->mu);
+    if (a >= 0.f && b >= a) S->windows.push_back({(double)a, (double)b});
     r.t_done = clk::now();
     r.done = true;
     r.points.clear();
@@ -170,6 +184,12 @@ void finish(gwn_server_s* S, Slot& sl) {
 
 void worker_loop(gwn_server_s* S) {
     cudaSetDevice(S->device);
+    // the time origin of the requests' device windows
+    if (cudaEventCreate(&S->ref) != cudaSuccess || cudaEventRecord(S->ref, 0) != cudaSuccess ||
+        cudaEventSynchronize(S->ref) != cudaSuccess) {
+        if (S->ref) cudaEventDestroy(S->ref);
+        S->ref = nullptr;  // windows are then not recorded
+    }
     while (true) {
         std::vector<std::pair<Slot*, std::shared_ptr<Request>>> todo;
         {
@@ -191,6 +211,9 @@ void worker_loop(gwn_server_s* S) {
                 todo.push_back({&sl, head});
                 S->queue.pop_front();
             }
+            int64_t busy = 0;
+            for (auto& sl : S->slots) busy += sl.cur ? 1 : 0;
+            S->max_in_flight = std::max(S->max_in_flight, busy);
         }
         for (auto& [sl, r] : todo) {
             gwn_status st = launch(S, *sl, *r);
@@ -348,6 +371,21 @@ gwn_status gwn_serve_stats(gwn_server S, gwn_server_stats* st) {
         st->queries_per_s = span > 0 ? S->points_done / span : 0.0;
     }
     st->budget_used_bytes = (int64_t)S->budget_used;
+    st->max_in_flight = S->max_in_flight;
+    // largest number of completed requests whose device windows overlapped
+    // (sweep over the window endpoints; an end sorts before a start at the same time)
+    std::vector<std::pair<double, int>> ev;
+    ev.reserve(S->windows.size() * 2);
+    for (auto& w : S->windows) {
+        ev.push_back({w.first, +1});
+        ev.push_back({w.second, -1});
+    }
+    std::sort(ev.begin(), ev.end());
+    int64_t cur = 0;
+    for (auto& e : ev) {
+        cur += e.second;
+        st->max_gpu_overlap = std::max(st->max_gpu_overlap, cur);
+    }
     return GWN_OK;
 }
 
@@ -365,8 +403,11 @@ gwn_status gwn_serve_destroy(gwn_server S) {
         if (sl.pin_in) cudaFreeHost(sl.pin_in);
         if (sl.pin_out) cudaFreeHost(sl.pin_out);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.t0) cudaEventDestroy(sl.t0);
+        if (sl.t1) cudaEventDestroy(sl.t1);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (S->ref) cudaEventDestroy(S->ref);
     delete S;
     return GWN_OK;
 }

@@ -4,7 +4,9 @@ resident 2D and 3D models with memory-budget admission.
 The property checked is that a request returns the same values and labels
 whether it runs alone or mixed with other requests (other models, sizes and
 point precisions) queued behind a small memory budget, and that those values
-are the ones the direct query entry point gives.
+are the ones the direct query entry point gives; in the mixed run, requests
+must have been in flight together and their device work must have overlapped
+(timing events around each request's work on its slot's stream).
 """
 import numpy as np
 import pytest
@@ -74,6 +76,10 @@ def test_serve_alone_equals_mixed_equals_direct(models):
     assert st["points_completed"] == sum(p.shape[0] for _, p in reqs)
     assert 0 < st["p50_ms"] <= st["p99_ms"]
     assert st["budget_used_bytes"] == 0
+    # continuous batching: requests were admitted while others were in flight,
+    # and their device work (copy in, query, copy out) overlapped on the GPU
+    assert st["max_in_flight"] >= 2
+    assert st["max_gpu_overlap"] >= 2
     srv.close()
 
     for (which, pts), (wa, la), (wm, lm) in zip(reqs, alone, mixed):

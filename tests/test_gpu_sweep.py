@@ -41,3 +41,49 @@ def test_error_falls_with_order_and_beta(dim):
         e = [_rows(rows, order=order, beta=b)[0]["max_abs_dgwn"] for b in (3.0, 6.0, 12.0)]
         assert e[0] > e[1] > e[2], (order, e)
     assert all(r["queries_per_s"] > 0 for r in rows)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_sweep_against_the_oracle(dim, oracle_lib):
+    """The sweep with the FP64 CPU oracle as its reference (seeded queries):
+    the default GPU reference agrees with the oracle, and the error of the
+    FP64 query falls with beta at order 2 against the oracle itself."""
+    if dim == 2:
+        prims, q = configs.star_2d(n_queries=8192)
+    else:
+        prims, q = configs.sphere_3d(n_queries=8192)
+    rng = np.random.default_rng(99 + dim)
+    q = q[np.sort(rng.choice(q.shape[0], size=2048 if dim == 2 else 512, replace=False))]
+    q = q.astype(np.float32).astype(np.float64)
+    ref, fl = (oracle_lib.gwn2d if dim == 2 else oracle_lib.gwn3d)(prims, q)
+    pts = torch.from_numpy(q).cuda()
+    gpu_ref = S.exact_reference(dim, prims, pts)
+    ok = np.isfinite(ref)
+    assert np.max(np.abs(gpu_ref[ok] - ref[ok])) <= 1e-9
+    rows = S.sweep(dim, prims, pts, orders=(2,), betas=(3.0, 6.0, 12.0), reps=1, precision=gwn.PREC_FP64,
+                   reference=ref)
+    e = [r["max_abs_dgwn"] for r in rows]
+    assert e[0] > e[1] > e[2], e
+    # at beta = 12 the order-2 far field is well inside the FP32 path's 1e-4
+    assert e[2] <= 5e-5, e
+
+
+def test_adaptive_beta_against_the_oracle(oracle_lib):
+    """Geometry-aware beta per cluster (build option adaptive_beta, the
+    per-cluster factor Section 5 names) on the nested-loop workload of
+    configuration 2: the FP32 + repair query against the oracle on a seeded
+    sample and on every query the GPU repaired or sent to the near band."""
+    from synth import geometry as G
+    curves, q = configs.loops_2d()
+    m = gwn.gwn_build_2d(curves, beta=12.0, adaptive_beta=1)
+    w, lab, st = m.query(torch.from_numpy(q).float().cuda())
+    w, lab, st = w.cpu().numpy(), lab.cpu().numpy(), st.cpu().numpy()
+    rng = np.random.default_rng(31)
+    idx = np.unique(np.concatenate([rng.choice(q.shape[0], 3000, replace=False),
+                                    np.flatnonzero(st & (gwn.QS_REPAIRED | gwn.QS_NEAR))[:1000]]))
+    lo, hi = G.shape_bbox_2d(curves)
+    w_ref, fl = oracle_lib.gwn2d(curves, q[idx], near_thr=1e-6 * float(np.linalg.norm(hi - lo)))
+    ok = np.isfinite(w_ref)
+    assert np.max(np.abs(w[idx][ok] - w_ref[ok])) <= 1e-4
+    keep = ok & ((fl & 1) == 0) & (np.abs((w_ref - np.floor(w_ref)) - 0.5) > 1e-6)
+    assert np.array_equal(lab[idx][keep], np.round(w_ref[keep]).astype(np.int32))

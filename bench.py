@@ -594,8 +594,9 @@ def main():
         serving = serving_leg(gwn, args.serve_seconds, log)
 
     # kernels per chunk of up to 2^19 points: bin, scan, scatter; 3 rounds of traversal, pair key, scan,
-    # pair scatter, pair eval (+ round switch x2); near band, overflow, finish, repair x3, counter accumulate
-    launches_per_step = sum(27 * math.ceil(p.shape[0] / (1 << 19)) for p in points)
+    # pair scatter, node-table pairs, full pairs (+ round switch x2); near band, overflow, finish, the
+    # chunk's own repair x3 (normally empty), counter accumulate; per query: repair x3 + its accumulate
+    launches_per_step = sum(30 * math.ceil(p.shape[0] / (1 << 19)) + 4 for p in points)
     line = {
         "metric": "GWN queries/s (batched containment, 16 trimmed-NURBS models)",
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),

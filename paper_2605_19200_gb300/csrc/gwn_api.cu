@@ -323,8 +323,8 @@ __device__ __forceinline__ double leaf64(const DevTree& t, int l, const double* 
 template <int DIM>
 __global__ void __launch_bounds__(128) k_repair(DevTree t, const void* pts, int dtype, QueryParams p, double* out_w,
                                                 int* out_label, uint32_t* out_status, const int* rlist,
-                                                const int* rcount) {
-    int cnt = *rcount;
+                                                const int* rcount, int cap = 0x7fffffff) {
+    int cnt = min(*rcount, cap);
     bool direct = p.mode == GWN_MODE_DIRECT || !(p.beta2_repair > 0);
     // the all-FP64 precision mode integrates to ~1e-8, the repair to ~1e-7
     const double ratio = p.precision == GWN_PREC_FP64 ? kRatio64Exact : kRatio64Repair;
@@ -391,6 +391,10 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     w.rw = (double*)carve(n * sizeof(double));
     w.pairs64 = (int2*)carve((dim != 2 ? n : 0) * sizeof(int2));
     w.rlist = (int*)carve(n * sizeof(int));
+    w.rlist_g = (int*)carve(n * sizeof(int));
+    w.rst = (uint32_t*)carve(n * sizeof(uint32_t));
+    w.gcount = (int*)carve(8 * sizeof(int));
+    w.rcap = (int)n;
     w.olist = (int*)carve((dim != 2 ? n : 0) * sizeof(int));
     w.olist2 = (int*)carve((dim != 2 ? n : 0) * sizeof(int));
     w.work = (unsigned long long*)carve(kWorkCount * sizeof(unsigned long long));
@@ -435,21 +439,10 @@ gwn_status ensure_workspace(gwn_model_s* m, size_t n, size_t stage_bytes) {
 
 }  // namespace
 
-// Enqueue the query kernels on `st` for device-resident points/outputs, using
-// workspace `ws` (sized for at least n points).  Shared with the batched and
-// serving entry points.
-static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
-                                uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const Workspace& ws) {
+// the kernels' parameters of one query
+static QueryParams query_params(const gwn_model_s* m, const gwn_query_opts& qo, const Workspace& ws) {
     QueryParams p;
     p.work = qo.count_work ? ws.work : nullptr;
-    const int pc = m->prof_chunks;
-    const bool prof = qo.profile != 0 && pc < gwn_model_s::kMaxProfChunks;
-    cudaEvent_t* ev = prof ? m->ev[pc] : nullptr;
-    if (prof) {
-        if (!ev[0])
-            for (int k = 0; k < 5; ++k) GWN_CUDA_TRY(cudaEventCreate(&ev[k]));
-        m->prof_chunks = pc + 1;
-    }
     double beta = qo.beta > 0 ? qo.beta : m->opts.beta;
     p.beta2 = (float)(beta * beta);
     double beta_leaf = qo.beta_leaf > 0 ? qo.beta_leaf : (m->opts.beta_leaf > 0 ? m->opts.beta_leaf : beta);
@@ -463,12 +456,64 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
     p.band = (float)(qo.repair_band > 0 ? qo.repair_band : m->opts.repair_band);
     p.mode = qo.mode;
     p.precision = qo.precision >= 0 ? qo.precision : m->opts.precision;
-    const int B = 128;
-    const int ni = (int)n;
-    const unsigned nb = (unsigned)((n + B - 1) / B);
+    return p;
+}
+
+static int device_sms() {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// FP64 re-evaluation (GWN_PREC_FP32_REPAIR) of the points in list R, whose
+// indices address pts and the outputs.  3D always goes through the warp
+// traversal and the FP64 pair list: with beta_repair = 0 or in direct mode
+// (exact sum over every leaf) every leaf becomes a pair, and the pairs of all
+// repaired points spread over the whole GPU instead of one warp walking all
+// leaves per point.
+static gwn_status enqueue_repair(gwn_model_s* m, const QueryParams& p, const void* pts, int dtype, const RepairList& R,
+                                 double* out_w, int* out_label, uint32_t* out_status, cudaStream_t st, int sms) {
+    const int B = 128;
+    const unsigned rb = (unsigned)(sms * 8);
+    const unsigned wb = (unsigned)(sms * 4);  // blocks of kRepairWarps warps, one warp per repaired point
+    if (m->dim == 2 && (p.mode == GWN_MODE_DIRECT || !(p.beta2_repair > 0))) {
+        k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, R.idx, R.count, R.cap);
+    } else if (m->dim == 2) {
+        k_rtrav_warp<2><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, p.beta2_repair, R, out_w, out_label,
+                                                         out_status);
+    } else {
+        const bool direct = p.mode == GWN_MODE_DIRECT;
+        k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, direct ? 0.0 : p.beta2_repair, R,
+                                                         out_w, out_label, out_status,
+                                                         direct ? 0.0 : p.beta2_repair_leaf);
+        k_rpairs3_warp<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, R);
+        k_rfinish<<<(unsigned)(sms * 2), B, 0, st>>>(R, out_w, out_label, out_status);
+    }
+    GWN_CUDA_TRY(cudaGetLastError());
+    return GWN_OK;
+}
+
+// Enqueue the query kernels of one chunk (points off .. off + n - 1 of the
+// query; pts and the outputs point at the chunk) on `st`, using workspace
+// `ws` (sized for at least n points).  Shared with the batched and serving
+// entry points through gwn_enqueue_device.
+static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size_t n, size_t off, double* out_w,
+                                int* out_label, uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st,
+                                const Workspace& ws) {
+    const QueryParams p = query_params(m, qo, ws);
+    const int pc = m->prof_chunks;
+    const bool prof = qo.profile != 0 && pc < gwn_model_s::kMaxProfChunks;
+    cudaEvent_t* ev = prof ? m->ev[pc] : nullptr;
+    if (prof) {
+        if (!ev[0])
+            for (int k = 0; k < 5; ++k) GWN_CUDA_TRY(cudaEventCreate(&ev[k]));
+        m->prof_chunks = pc + 1;
+    }
+    const int B = 128;
+    const int ni = (int)n;
+    const unsigned nb = (unsigned)((n + B - 1) / B);
+    const int sms = device_sms();
     if (p.precision == GWN_PREC_FP64) {
         if (p.mode == GWN_MODE_DIRECT) {
             // exact FP64 direct sum, one warp per point (lanes stride over the leaves)
@@ -561,31 +606,17 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         }
         GWN_CUDA_TRY(cudaGetLastError());
         // 4. outputs and the repair list
-        k_finish<<<nb, B, 0, st>>>(ni, ws.wacc, ws.st, p.precision, p.band, out_w, out_label, out_status, ws.rlist, rcount);
+        k_finish<<<nb, B, 0, st>>>(ni, ws.wacc, ws.st, p.precision, p.band, out_w, out_label, out_status, ws.rlist,
+                                   rcount, (int)off, ws.rlist_g, ws.gcount, ws.rcap);
         GWN_CUDA_TRY(cudaGetLastError());
     }
     if (p.precision == GWN_PREC_FP32_REPAIR) {
-        unsigned rb = (unsigned)std::min<long long>(std::max<long long>(nb, sms * 4), (long long)sms * 8);
-        if (rb == 0) rb = 1;
-        const unsigned wb = (unsigned)(sms * 4);  // blocks of kRepairWarps warps, one warp per repaired point
-        // 3D always goes through the warp traversal and the FP64 pair list: with
-        // beta_repair = 0 or in direct mode (exact sum over every leaf) every leaf
-        // becomes a pair, and the pairs of all repaired points spread over the
-        // whole GPU instead of one warp walking all leaves per point
-        if (m->dim == 2 && (p.mode == GWN_MODE_DIRECT || !(p.beta2_repair > 0))) {
-            k_repair<2><<<rb, B, 0, st>>>(m->tree, pts, dtype, p, out_w, out_label, out_status, ws.rlist, rcount);
-        } else if (m->dim == 2) {
-            k_rtrav_warp<2><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, p.beta2_repair, ws.rlist, ws, out_w,
-                                                             out_label, out_status);
-        } else {
-            const bool direct = p.mode == GWN_MODE_DIRECT;
-            k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, direct ? 0.0 : p.beta2_repair,
-                                                             ws.rlist, ws, out_w, out_label, out_status,
-                                                             direct ? 0.0 : p.beta2_repair_leaf);
-            k_rpairs3_warp<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.rlist, ws);
-            k_rfinish<<<(unsigned)(sms * 2), B, 0, st>>>(ws.rlist, ws, out_w, out_label, out_status);
-        }
-        GWN_CUDA_TRY(cudaGetLastError());
+        // points of this chunk that did not fit the query's repair list (normally
+        // none: the list holds as many points as a chunk), repaired right away;
+        // direct mode, whose k_query32 lists every point locally, too
+        const RepairList R{ws.rlist, rcount, ws.rcap, ws.rw, ws.rst, ws.rpairs, ws.counters + 4};
+        gwn_status s = enqueue_repair(m, p, pts, dtype, R, out_w, out_label, out_status, st, sms);
+        if (s != GWN_OK) return s;
     }
     k_accum<<<1, 32, 0, st>>>(ws);
     GWN_CUDA_TRY(cudaGetLastError());
@@ -601,12 +632,24 @@ gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t
     if (qo.count_work) GWN_CUDA_TRY(cudaMemsetAsync(ws.work, 0, kWorkCount * sizeof(unsigned long long), st));
     m->prof_chunks = 0;
     m->profiled = qo.profile != 0;
+    GWN_CUDA_TRY(cudaMemsetAsync(ws.gcount, 0, 8 * sizeof(int), st));
     for (size_t off = 0; off < n; off += kChunk) {
         size_t c = std::min(kChunk, n - off);
-        gwn_status s = enqueue_chunk(m, reinterpret_cast<const char*>(pts) + off * esz, dtype, c, out_w + off,
+        gwn_status s = enqueue_chunk(m, reinterpret_cast<const char*>(pts) + off * esz, dtype, c, off, out_w + off,
                                      out_label ? out_label + off : nullptr, out_status ? out_status + off : nullptr,
                                      qo, st, ws);
         if (s != GWN_OK) return s;
+    }
+    // one FP64 repair pass over the points that every chunk listed (indices into
+    // the whole query), so that the repair fills the GPU instead of running a
+    // few warps after each chunk
+    const QueryParams p = query_params(m, qo, ws);
+    if (p.precision == GWN_PREC_FP32_REPAIR && p.mode == GWN_MODE_BVH) {
+        const RepairList R{ws.rlist_g, ws.gcount, ws.rcap, ws.rw, ws.rst, ws.rpairs, ws.gcount + 1};
+        gwn_status s = enqueue_repair(m, p, pts, dtype, R, out_w, out_label, out_status, st, device_sms());
+        if (s != GWN_OK) return s;
+        k_accum_repair<<<1, 32, 0, st>>>(ws);
+        GWN_CUDA_TRY(cudaGetLastError());
     }
     return GWN_OK;
 }

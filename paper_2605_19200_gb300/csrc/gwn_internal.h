@@ -165,8 +165,21 @@ struct QueryParams {
     int precision;             // GWN_PREC_*
 };
 
-constexpr long long kRepairPairCap = 1ll << 22;  // FP64 repair pairs per chunk
+constexpr long long kRepairPairCap = 1ll << 22;  // FP64 repair pairs per repair pass
 constexpr int kCounterCount = 16;                // device counters of one chunk
+
+// The points of one FP64 repair pass and its scratch.  The list holds point
+// indices into the arrays the repair kernels are given; count may exceed cap
+// (entries past cap were not stored and are not repaired by this pass).
+struct RepairList {
+    const int* idx;
+    const int* count;
+    int cap;
+    double* rw;         // FP64 sum per entry (3D: far field and in-place leaves, then the pairs)
+    uint32_t* rst;      // status bits per entry (3D)
+    int2* pairs;        // FP64 (entry, leaf) pairs (3D), kRepairPairCap
+    int* npairs;        // their count
+};
 
 // Scratch of one in-flight query (one chunk of points), carved from one
 // device allocation (see workspace_layout in gwn_api.cu).
@@ -189,7 +202,11 @@ struct Workspace {
     int* olist2;      // n
     unsigned long long* work;  // kWorkCount counters
     unsigned long long* acc;   // per-query totals of the counters over all chunks
-    int* rlist;       // n
+    int* rlist;       // n: points of this chunk to repair that did not fit the query's list
+    int* rlist_g;     // n: the query's points to repair (indices into the whole query), one pass after its last chunk
+    uint32_t* rst;    // n: status bits per repair-list entry
+    int* gcount;      // [0] entries of rlist_g, [1] FP64 pairs of its pass (cleared once per query)
+    int rcap;         // entries of rlist_g (= the points a workspace holds)
     long long pair_cap;
 };
 

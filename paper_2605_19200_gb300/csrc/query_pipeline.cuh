@@ -461,8 +461,12 @@ __global__ void __launch_bounds__(128) k_trav2(DevTree t, const void* pts, int d
     if (work) flush_work(wl, work);
 }
 
+// outputs of one chunk (points off .. off + n - 1 of the query); points to
+// repair go to the query's list (index off + i) while it has room, else to the
+// chunk's own list (index i), repaired right after the chunk
 __global__ void k_finish(int n, const float* wacc, const uint32_t* stv, int precision, float band, double* out_w,
-                         int* out_label, uint32_t* out_status, int* rlist, int* rcount) {
+                         int* out_label, uint32_t* out_status, int* rlist, int* rcount, int off, int* rlist_g,
+                         int* gcount, int gcap) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double w = (double)wacc[i];
@@ -470,8 +474,13 @@ __global__ void k_finish(int n, const float* wacc, const uint32_t* stv, int prec
     if (precision == GWN_PREC_FP32_REPAIR) {
         double fr = w - floor(w);
         if (fabs(fr - 0.5) < (double)band || (st & (GWN_QS_STACK_OVERFLOW | GWN_QS_UNRESOLVED))) {
-            int slot = atomicAdd(rcount, 1);
-            rlist[slot] = i;
+            int slot = atomicAdd(gcount, 1);
+            if (slot < gcap) {
+                rlist_g[slot] = off + i;
+            } else {
+                slot = atomicAdd(rcount, 1);
+                rlist[slot] = i;
+            }
         }
     }
     out_w[i] = w;
@@ -484,14 +493,13 @@ __global__ void k_finish(int n, const float* wacc, const uint32_t* stv, int prec
 namespace gwn {
 
 // FP64 repair pairs with one warp per pair (leaf3_warp64)
-__global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts, int dtype, const int* rlist,
-                                                      Workspace ws) {
+__global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts, int dtype, RepairList R) {
     __shared__ int2 sstk[4][kQuadStack];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long np = min((long long)ws.counters[4], kRepairPairCap);
+    const long long np = min((long long)*R.npairs, kRepairPairCap);
     for (long long j = (long long)blockIdx.x * 4 + wid; j < np; j += (long long)gridDim.x * 4) {
-        const int2 pr = ws.rpairs[j];
-        const int qi = rlist[pr.x];
+        const int2 pr = R.pairs[j];
+        const int qi = R.idx[pr.x];
         double q[3];
         if (dtype == GWN_F32) {
             const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * 3;
@@ -504,8 +512,8 @@ __global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts
         const bool ok = leaf_fits_w4(t, pr.y) ? leaf3_warp64<4>(t, pr.y, q, kRatio64RepairW4, kLevel64, sstk[wid], &v)
                                               : leaf3_warp64<8>(t, pr.y, q, kRatio64Repair, kLevel64, sstk[wid], &v);
         if (lane == 0) {
-            if (ok) atomicAdd(&ws.rw[pr.x], v);
-            else atomicOr(&ws.st[qi], GWN_QS_UNRESOLVED);
+            if (ok) atomicAdd(&R.rw[pr.x], v);
+            else atomicOr(&R.rst[pr.x], GWN_QS_UNRESOLVED);
         }
         __syncwarp();
     }
@@ -529,14 +537,23 @@ __global__ void k_accum(Workspace ws) {
     if (threadIdx.x < kCounterCount) ws.acc[threadIdx.x] += (unsigned long long)ws.counters[threadIdx.x];
 }
 
-__global__ void k_rfinish(const int* rlist, Workspace ws, double* out_w, int* out_label, uint32_t* out_status) {
-    int cnt = ws.counters[1];
+// the query-wide repair pass in the totals: repaired points and FP64 pairs
+__global__ void k_accum_repair(Workspace ws) {
+    if (threadIdx.x == 0) {
+        ws.acc[1] += (unsigned long long)min(ws.gcount[0], ws.rcap);
+        ws.acc[4] += (unsigned long long)ws.gcount[1];
+    }
+}
+
+// repaired values, labels and status (the FP32 status bits k_finish wrote are kept)
+__global__ void k_rfinish(RepairList R, double* out_w, int* out_label, uint32_t* out_status) {
+    const int cnt = min(*R.count, R.cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-        int qi = rlist[k];
-        double w = ws.rw[k];
+        int qi = R.idx[k];
+        double w = R.rw[k];
         out_w[qi] = w;
         if (out_label) out_label[qi] = (int)round(w);
-        if (out_status) out_status[qi] = ws.st[qi] | GWN_QS_REPAIRED;
+        if (out_status) out_status[qi] |= R.rst[k] | GWN_QS_REPAIRED;
     }
 }
 
@@ -556,18 +573,17 @@ constexpr int kRepairWarps = 4;  // warps per block
 
 template <int DIM>
 __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, const void* pts, int dtype, double beta2r,
-                                                                  const int* rlist, Workspace ws, double* out_w,
-                                                                  int* out_label, uint32_t* out_status,
-                                                                  double beta2rl = -1.0) {
+                                                                  RepairList R, double* out_w, int* out_label,
+                                                                  uint32_t* out_status, double beta2rl = -1.0) {
     if (beta2rl < 0) beta2rl = beta2r;  // leaves' far test (3D): default the nodes' factor
     __shared__ int sstack[kRepairWarps][kWarpStack];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kRepairWarps + wid;
     const int nw = gridDim.x * kRepairWarps;
-    const int cnt = ws.counters[1];
+    const int cnt = min(*R.count, R.cap);
     int* stk = sstack[wid];
     for (int k = gw; k < cnt; k += nw) {
-        const int qi = rlist[k];
+        const int qi = R.idx[k];
         double q[3] = {0, 0, 0};
         if (dtype == GWN_F32) {
             const float* p = reinterpret_cast<const float*>(pts) + (size_t)qi * DIM;
@@ -598,8 +614,8 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
                         if (beta2rl > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2rl * h[3]) {
                             acc += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
                         } else {
-                            int slot = atomicAdd(&ws.counters[4], 1);
-                            if (slot < kRepairPairCap) ws.rpairs[slot] = make_int2(k, li);
+                            int slot = atomicAdd(R.npairs, 1);
+                            if (slot < kRepairPairCap) R.pairs[slot] = make_int2(k, li);
                             else acc += leaf3_eval64(t, li, q[0], q[1], q[2], st, kRatio64Repair);
                         }
                     }
@@ -642,10 +658,10 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
             if (DIM == 2) {
                 out_w[qi] = acc;
                 if (out_label) out_label[qi] = (int)round(acc);
-                if (out_status) out_status[qi] = ws.st[qi] | st | GWN_QS_REPAIRED;
+                if (out_status) out_status[qi] |= st | GWN_QS_REPAIRED;
             } else {
-                ws.rw[k] = acc;
-                ws.st[qi] = st;
+                R.rw[k] = acc;
+                R.rst[k] = st;
             }
         }
         __syncwarp();

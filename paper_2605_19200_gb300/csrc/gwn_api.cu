@@ -370,8 +370,8 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     const long long cap = dim != 2 ? (long long)n * 96 + 65536 : 0;
     const size_t cells2 = (size_t)1 << (2 * kBinBits2), cells3 = (size_t)1 << (3 * kBinBits3);
     const size_t cells = dim == 2 ? cells2 : dim == 3 ? cells3 : std::max(cells2, cells3);
-    const size_t hist = std::max(cells, (size_t)n_leaves) + 1;
-    const size_t keyn = std::max((size_t)n, (size_t)cap);
+    const size_t hist = cells + 1;
+    const size_t keyn = n;
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         char* p = base ? base + off : nullptr;
@@ -385,7 +385,7 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     w.wacc = (float*)carve(n * sizeof(float));
     w.st = (uint32_t*)carve(n * sizeof(uint32_t));
     w.pairs = (int2*)carve((size_t)cap * sizeof(int2));
-    w.pairs2 = (int2*)carve((size_t)cap * sizeof(int2));
+    w.pairs2 = (int2*)carve((size_t)cap * sizeof(int2));  // pairs left to the full evaluator
     w.counters = (int*)carve(kCounterCount * sizeof(int));
     w.rpairs = (int2*)carve((dim != 2 ? (size_t)kRepairPairCap : 0) * sizeof(int2));
     w.rw = (double*)carve(n * sizeof(double));
@@ -572,7 +572,6 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         } else {
             // rounds: round 0 over all points; rounds 1, 2 over the points whose
             // (point, leaf) pairs did not fit the list in the previous round
-            const unsigned pb = (unsigned)std::max(1, sms * 16);
             for (int round = 0; round < 3; ++round) {
                 const int* list = round == 0 ? perm : (round == 1 ? ws.olist : ws.olist2);
                 int* olist_out = round == 1 ? ws.olist2 : ws.olist;
@@ -580,19 +579,14 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
                                           round == 0 ? nullptr : ws.counters + 5, olist_out);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
                 GWN_CUDA_TRY(cudaGetLastError());
-                // 3. exact leaves, grouped by leaf
-                GWN_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, (size_t)m->host.n_leaves * sizeof(int), st));
-                k_pair_key<<<pb, 256, 0, st>>>(ws.pair_cap, ws.counters, ws.pairs, ws.key, ws.hist);
-                k_scan<<<1, 1024, 0, st>>>(ws.hist, m->host.n_leaves);
-                k_pair_scatter<<<pb, 256, 0, st>>>(ws.pair_cap, ws.counters, ws.pairs, ws.key, ws.hist, ws.pairs2);
+                // 3. exact leaves (the list comes in runs of one leaf): far pairs from
+                // the node tables; the rest, in list order, to the full evaluator
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[2], st));
-                // far pairs from the node tables; the rest, in leaf order, to the full
-                // evaluator (ws.pairs is free again once the sorted copy exists)
                 k_pair_fast<<<(unsigned)(sms * 16), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters,
-                                                                ws.pairs2, ws.wacc, ws.st, ws.pairs, p.work);
+                                                                ws.pairs, ws.wacc, ws.st, ws.pairs2, p.work);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[4], st));
                 k_pair_eval<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters + 8,
-                                                               ws.counters, ws.pairs, ws.wacc, ws.st, ws.pairs64, ni,
+                                                               ws.counters, ws.pairs2, ws.wacc, ws.st, ws.pairs64, ni,
                                                                p.work);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[3], st));
                 if (round < 2) k_next_round<<<1, 32, 0, st>>>(ws);

@@ -188,12 +188,12 @@ struct Workspace {
     int2* rpairs;     // FP64 repair pairs (kRepairPairCap, 3D)
     double* rw;       // FP64 repair accumulators (n)
     int* perm;        // n
-    int* key;         // max(n, pair capacity)
-    int* hist;        // max(cells, n_leaves) + 1
+    int* key;         // n: Morton cell of each point (binning)
+    int* hist;        // cells + 1
     float* wacc;      // n
     uint32_t* st;     // n
-    int2* pairs;      // pair capacity
-    int2* pairs2;     // pair capacity (sorted)
+    int2* pairs;      // pair capacity: (point, leaf) pairs of the traversal, in runs of one leaf
+    int2* pairs2;     // pair capacity: those left to the full evaluator
     int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
                       // [5] overflowed points of the current round (list input), [6] total overflow,
                       // [7] pairs of finished rounds, [8] pairs left to the full evaluator this round,

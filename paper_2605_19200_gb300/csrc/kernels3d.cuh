@@ -783,8 +783,17 @@ __device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3],
 template <typename T>
 GWN_HD inline T far3_eval(const T* f, T rx, T ry, T rz) {
     T r2 = rx * rx + ry * ry + rz * rz;
-    T i2 = T(1) / r2;
-    T i3 = i2 * Num<T>::rsqrt_(r2);
+    T i2, i3;
+    if (sizeof(T) == 4) {
+        // both inverse powers from one reciprocal square root (no division):
+        // relative error of a few ulp, far below the Taylor remainder
+        const T rs = Num<T>::rsqrt_(r2);
+        i2 = rs * rs;
+        i3 = i2 * rs;
+    } else {
+        i2 = T(1) / r2;
+        i3 = i2 * Num<T>::rsqrt_(r2);
+    }
     T t0 = f[0] * rx + f[1] * ry + f[2] * rz + f[3];
     T xx = rx * rx, yy = ry * ry, zz = rz * rz;
     T t1 = f[4] * xx + f[5] * yy + f[6] * zz + f[7] * rx * ry + f[8] * rx * rz + f[9] * ry * rz + f[10] * rx + f[11] * ry +

@@ -8,13 +8,14 @@
 //     (Eq. 3) to each point's accumulator.  2D leaves are evaluated in place
 //     (one atan2 unless the point is inside the leaf's box).  3D leaves that
 //     need the exact evaluation are not evaluated in the traversal: the
-//     (point, leaf) pair is appended to a work list, with one atomic per warp;
+//     (point, leaf) pairs are appended to a work list through a per-warp
+//     shared-memory buffer, one atomic per 128 pairs;
 //     points whose pairs do not fit are traversed again in up to two more
 //     rounds.
-//  3. 3D only: the work list is counting-sorted by leaf, and one thread per pair
-//     evaluates the leaf in FP32 and adds it to the point's accumulator.
-//     Consecutive threads now share the same leaf, so a warp reads one set of
-//     boundary curves.  Far pairs whose panels stop at level 0 or 1 (nearly
+//  3. 3D only: one thread per pair evaluates the leaf in FP32 and adds it to
+//     the point's accumulator.  The traversal writes each leaf's pairs in one
+//     run, so consecutive threads share the leaf and a warp reads one or two
+//     sets of boundary curves.  Far pairs whose panels stop at level 0 or 1 (nearly
 //     all) read the curves' query-independent node tables (k_pair_fast); the
 //     rest take the full evaluation (k_pair_eval: foot-point search, adaptive
 //     panels from the Bernstein form).  Pairs FP32 cannot resolve go to the
@@ -32,7 +33,6 @@ namespace gwn {
 
 constexpr int kBinBits2 = 9;   // 512 x 512 cells in 2D
 constexpr int kBinBits3 = 5;   // 32^3 cells in 3D
-constexpr int kPairLocal = 8;  // pairs a thread buffers before reserving space
 constexpr uint32_t kPairOverflow = 0x100u;  // internal status bit: the point's pairs did not fit
 
 
@@ -121,25 +121,27 @@ __global__ void k_scatter_perm(int n, const int* key, int* cursor, int* perm) {
     perm[pos] = i;
 }
 
-// append (point, leaf) pairs from a converged warp: one atomic per warp.  If
-// the list is full the point is flagged; such points skip the pair pass and are
-// evaluated again, leaves in place, by k_overflow3.
-__device__ __forceinline__ void flush_pairs(int2* local, int cnt, Workspace ws, uint32_t& st, unsigned mask) {
-    int lane = threadIdx.x & 31;
-    int incl = cnt;
-    for (int off = 1; off < 32; off <<= 1) {
-        int v = __shfl_up_sync(mask, incl, off);
-        if (lane >= off) incl += v;
-    }
-    int total = __shfl_sync(mask, incl, 31);
+constexpr int kPairBuf = 128;  // (point, leaf) pairs buffered per warp in shared memory
+
+// write a warp's buffered pairs (n of them, warp-uniform) to the pair list with
+// one atomic and coalesced stores.  If the list is full, the lanes that own the
+// entries which did not fit are added to `ovf` (every lane gets the same mask);
+// their points skip the pair pass and are traversed again in the next round.
+__device__ __forceinline__ void flush_warp_pairs(const int2* buf, const unsigned char* own, int n, const Workspace& ws,
+                                                 unsigned& ovf) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     int base = 0;
-    if (lane == 31 && total > 0) base = atomicAdd(&ws.counters[0], total);
-    base = __shfl_sync(mask, base, 31);
-    long long start = (long long)base + incl - cnt;
-    for (int k = 0; k < cnt; ++k) {
-        if (start + k < ws.pair_cap) ws.pairs[start + k] = local[k];
-        else st |= kPairOverflow;
+    if (lane == 0 && n > 0) base = atomicAdd(&ws.counters[0], n);
+    base = __shfl_sync(full, base, 0);
+    unsigned lost = 0;
+    for (int j = lane; j < n; j += 32) {
+        const long long pos = (long long)base + j;
+        if (pos < ws.pair_cap) ws.pairs[pos] = buf[j];
+        else lost |= 1u << own[j];
     }
+    for (int off = 16; off > 0; off >>= 1) lost |= __shfl_xor_sync(full, lost, off);
+    ovf |= lost;
 }
 
 // traversal with deferred 3D leaves, one packet per warp: the 32 queries of a
@@ -151,9 +153,13 @@ __device__ __forceinline__ void flush_pairs(int2* local, int cnt, Workspace ws, 
 // loads are then the same address for the whole warp, and lanes never wait on
 // each other's different branches.  Binned queries share most of their paths
 // (the union of a warp's visits is ~1.05x the longest single path), so the
-// packet costs little extra work.  Exact 3D leaves go to the pair list (warp-
-// wide flushes); every thread of the grid reaches them (lanes past the end of
-// the list take part with an empty mask).
+// packet costs little extra work.  Exact 3D leaves go to the pair list: at a
+// leaf, the lanes that need it exactly write their (point, leaf) pairs next to
+// each other into the warp's shared-memory buffer, which is flushed to the list
+// with one atomic when full, so the list comes out in runs of one leaf (the
+// pair kernels read a leaf's data once per run, with no sort by leaf).  Every
+// thread of the grid reaches the flushes (lanes past the end of the list take
+// part with an empty mask).
 // n_dev != nullptr: the point list `perm` holds *n_dev entries (a later round
 // over the points whose pairs overflowed; their indices go to `olist_out`)
 constexpr int kPacketStack = 96;  // entries per warp
@@ -162,9 +168,13 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
                                                float beta2, float beta2l, Workspace ws, unsigned long long* work,
                                                const int* n_dev, int* olist_out) {
     __shared__ int2 sstk[4][kPacketStack];
+    __shared__ int2 sbuf[4][kPairBuf];
+    __shared__ unsigned char sown[4][kPairBuf];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     int2* stk = sstk[threadIdx.x >> 5];
+    int2* buf = sbuf[threadIdx.x >> 5];
+    unsigned char* own = sown[threadIdx.x >> 5];
     WorkLocal wl = {};
     if (n_dev) n = *n_dev;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,8 +185,8 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
     if (active) load_point_f(pts, dtype, 3, qi, q);
     float w = 0.f;
     uint32_t st = 0;
-    int2 local[kPairLocal];
-    int cnt = 0;
+    int bcnt = 0;                      // warp-uniform: entries in buf
+    unsigned ovf = 0;                  // lanes with pairs that did not fit the list
     int sp = 0;                        // warp-uniform
     int node = t.root;                 // warp-uniform
     unsigned mask = __ballot_sync(full, active);
@@ -192,13 +202,22 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
             if (far) {
                 if (work) wl.v[kWorkFar] += 1;
                 w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
-            } else if (mine) {
-                local[cnt++] = make_int2(qi, li);
             }
-            // flush when any lane's buffer is full (warp-uniform decision)
-            if (__any_sync(full, cnt == kPairLocal)) {
-                flush_pairs(local, cnt, ws, st, full);
-                cnt = 0;
+            const unsigned need = __ballot_sync(full, mine && !far);
+            if (need) {
+                const int nn = __popc(need);
+                if (bcnt + nn > kPairBuf) {
+                    __syncwarp();
+                    flush_warp_pairs(buf, own, bcnt, ws, ovf);
+                    bcnt = 0;
+                    __syncwarp();
+                }
+                if ((need >> lane) & 1u) {
+                    const int pos = bcnt + __popc(need & ((1u << lane) - 1u));
+                    buf[pos] = make_int2(qi, li);
+                    own[pos] = (unsigned char)lane;
+                }
+                bcnt += nn;
             }
         } else {
             const float4 h = GWN_LDG(t.hdr + node);
@@ -233,7 +252,9 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
             __syncwarp();
         }
     }
-    flush_pairs(local, cnt, ws, st, full);
+    __syncwarp();
+    flush_warp_pairs(buf, own, bcnt, ws, ovf);
+    if ((ovf >> lane) & 1u) st |= kPairOverflow;
     if (active) {
         ws.wacc[qi] = w;
         ws.st[qi] = st;
@@ -257,27 +278,9 @@ __global__ void __launch_bounds__(128) k_overflow3(DevTree t, const void* pts, i
     }
 }
 
-__global__ void k_pair_key(long long npair_cap, const int* counters, const int2* pairs, int* key, int* hist) {
-    long long np = min((long long)counters[0], npair_cap);
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
-        int leaf = pairs[k].y;
-        key[k] = leaf;
-        atomicAdd(&hist[leaf], 1);
-    }
-}
-
-__global__ void k_pair_scatter(long long npair_cap, const int* counters, const int2* pairs, const int* key, int* cursor,
-                               int2* out) {
-    long long np = min((long long)counters[0], npair_cap);
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
-        int pos = atomicAdd(&cursor[key[k]], 1);
-        out[pos] = pairs[k];
-    }
-}
-
 // exact 3D leaves from the node tables, one thread per (point, leaf) pair in
-// leaf order (the 32 pairs of a warp mostly share one leaf, so its table is
-// read once for the warp): pairs whose point lies outside the leaf's
+// list order (runs of one leaf, so the 32 pairs of a warp mostly share one or
+// two leaves and their tables are read once for the warp): pairs whose point lies outside the leaf's
 // 1.1-radius sphere and whose panels stop at level 0 or 1 add their value
 // here (leaf3_fast32).  The others -- points near the leaf, whose string needs
 // the foot-point search, and curves that need deeper panels -- are appended in

@@ -46,6 +46,7 @@ struct HostModel {
     std::vector<float4> c3pts;
     std::vector<double> c3pts64;
     std::vector<float4> c3n;       // kC3NodeVec per boundary curve
+    std::vector<double> c3n64;     // kC3Node64 per boundary curve
     std::vector<float4> c2;
     std::vector<double> c2_64;
     std::vector<float> c2mult;

@@ -587,6 +587,33 @@ void node_table(const std::vector<double>& X, int D, const float cen[3], float m
     out[0] = float4{len[0], len[1], len[2], mult};
 }
 
+// the FP64 node table of one boundary curve (kC3Node64 in gwn_internal.h):
+// absolute positions and tangents at the 8 Gauss-Legendre nodes of the level-0
+// panel and of the two level-1 panels, and the panels' length estimates with
+// the 8-point rule's span factor 1.1 (as the FP64 kernels compute them)
+void node_table64(const std::vector<double>& X, int D, double mult, const std::vector<double>& x8, double* out) {
+    const double a0[3] = {0.0, 0.0, 0.5}, hh[3] = {1.0, 0.5, 0.5};
+    for (int p = 0; p < 3; ++p) {
+        double* nodes = out + 4 + 48 * p;
+        double prev[3] = {0, 0, 0}, L = 0;
+        for (int k = 0; k < 8; ++k) {
+            double P[4], dP[4];
+            bez4_eval(X, D, a0[p] + hh[p] * x8[k], P, dP);
+            for (int c = 0; c < 3; ++c) {
+                const double x = P[c] / P[3];
+                nodes[6 * k + c] = x;
+                nodes[6 * k + 3 + c] = (dP[c] - x * dP[3]) / P[3];
+            }
+            const double* x = nodes + 6 * k;
+            if (k > 0) L += std::sqrt((x[0] - prev[0]) * (x[0] - prev[0]) + (x[1] - prev[1]) * (x[1] - prev[1]) +
+                                      (x[2] - prev[2]) * (x[2] - prev[2]));
+            for (int c = 0; c < 3; ++c) prev[c] = x[c];
+        }
+        out[p] = 1.1 * L;
+    }
+    out[3] = mult;
+}
+
 // compose a local (u, v) piece with the bicubic net: 4D rational Bezier of degree 6 deg
 void compose(const TP& p, const Net& N, std::vector<double>* X) {
     int d = p.deg;
@@ -877,8 +904,9 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
     out->net3.resize((size_t)nl * kNet3Vec);
     out->net3_64.resize((size_t)nl * 64);
     std::vector<double> X;
-    std::vector<double> g4x, g4w;  // the FP32 rule: node tables and minimum levels
+    std::vector<double> g4x, g4w, g8x, g8w;  // the FP32 rule (tables, minimum levels) and the FP64 rule
     gauss_legendre01(4, &g4x, &g4w);
+    gauss_legendre01(8, &g8x, &g8w);
     for (int i = 0; i < nl; ++i) {
         const Leaf& L = leaves[perm[i]];
         out->leaf_prim[i] = L.prim;
@@ -918,6 +946,9 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
                 float4 tab[kC3NodeVec];
                 node_table(X, D, cen, ci.mult, g4x, tab);
                 out->c3n.insert(out->c3n.end(), tab, tab + kC3NodeVec);
+                double tab64[kC3Node64];
+                node_table64(X, D, (double)L.mult[b], g8x, tab64);
+                out->c3n64.insert(out->c3n64.end(), tab64, tab64 + kC3Node64);
             }
             // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i),
             // then the same 2 D + 1 points of the reversed curve (evaluation for t > 1/2);

@@ -197,6 +197,7 @@ gwn_status upload_model(gwn_model_s* m) {
     UP(c3pts, c3pts);
     UP(c3pts64, c3pts64);
     UP(c3n, c3n);
+    UP(c3n64, c3n64);
     UP(c2, c2);
     UP(c2_64, c2_64);
     UP(c2mult, c2mult);
@@ -388,6 +389,7 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     w.pairs2 = (int2*)carve((size_t)cap * sizeof(int2));  // pairs left to the full evaluator
     w.counters = (int*)carve(kCounterCount * sizeof(int));
     w.rpairs = (int2*)carve((dim != 2 ? (size_t)kRepairPairCap : 0) * sizeof(int2));
+    w.rpairs2 = (int2*)carve((dim != 2 ? (size_t)kRepairPairCap : 0) * sizeof(int2));
     w.rw = (double*)carve(n * sizeof(double));
     w.pairs64 = (int2*)carve((dim != 2 ? n : 0) * sizeof(int2));
     w.rlist = (int*)carve(n * sizeof(int));
@@ -487,6 +489,7 @@ static gwn_status enqueue_repair(gwn_model_s* m, const QueryParams& p, const voi
         k_rtrav_warp<3><<<wb, 32 * kRepairWarps, 0, st>>>(m->tree, pts, dtype, direct ? 0.0 : p.beta2_repair, R,
                                                          out_w, out_label, out_status,
                                                          direct ? 0.0 : p.beta2_repair_leaf);
+        k_rpairs3_fast<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, R);
         k_rpairs3_warp<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, R);
         k_rfinish<<<(unsigned)(sms * 2), B, 0, st>>>(R, out_w, out_label, out_status);
     }
@@ -608,7 +611,8 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         // points of this chunk that did not fit the query's repair list (normally
         // none: the list holds as many points as a chunk), repaired right away;
         // direct mode, whose k_query32 lists every point locally, too
-        const RepairList R{ws.rlist, rcount, ws.rcap, ws.rw, ws.rst, ws.rpairs, ws.counters + 4};
+        const RepairList R{ws.rlist, rcount, ws.rcap, ws.rw, ws.rst, ws.rpairs, ws.counters + 4, ws.rpairs2,
+                           ws.counters + 10};
         gwn_status s = enqueue_repair(m, p, pts, dtype, R, out_w, out_label, out_status, st, sms);
         if (s != GWN_OK) return s;
     }
@@ -639,7 +643,8 @@ gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t
     // few warps after each chunk
     const QueryParams p = query_params(m, qo, ws);
     if (p.precision == GWN_PREC_FP32_REPAIR && p.mode == GWN_MODE_BVH) {
-        const RepairList R{ws.rlist_g, ws.gcount, ws.rcap, ws.rw, ws.rst, ws.rpairs, ws.gcount + 1};
+        const RepairList R{ws.rlist_g, ws.gcount, ws.rcap, ws.rw, ws.rst, ws.rpairs, ws.gcount + 1, ws.rpairs2,
+                           ws.gcount + 2};
         gwn_status s = enqueue_repair(m, p, pts, dtype, R, out_w, out_label, out_status, st, device_sms());
         if (s != GWN_OK) return s;
         k_accum_repair<<<1, 32, 0, st>>>(ws);
@@ -1142,7 +1147,7 @@ gwn_status gwn_model_tree(gwn_model m, int32_t* child, double* x0, double* r, do
 
 namespace {
 constexpr char kModelMagic[8] = {'G', 'W', 'N', 'M', 'O', 'D', 'E', 'L'};
-constexpr uint32_t kModelVersion = 2;
+constexpr uint32_t kModelVersion = 3;
 
 template <typename V>
 bool write_vec(FILE* f, const std::vector<V>& v) {
@@ -1197,6 +1202,7 @@ bool host_model_consistent(const HostModel& H, int dim) {
     if (dim == 2) return H.leaf2.size() == nl * kLeaf2Vec && H.leaf2_64.size() == nl * kLeaf2F64;
     if (H.leaf3.size() != nl || H.net3.size() != nl * kNet3Vec || H.net3_64.size() != nl * 64 ||
         H.c3pts64.size() != H.c3pts.size() * 4 || H.c3n.size() != H.c3.size() * kC3NodeVec ||
+        H.c3n64.size() != H.c3.size() * kC3Node64 ||
         H.c2.size() != H.c2mult.size() * kC2Vec ||
         H.c2_64.size() != H.c2mult.size() * 12)
         return false;
@@ -1217,7 +1223,7 @@ bool each_array(HostModel& H, F f) {
     return f(H.child) && f(H.hdr) && f(H.mom) && f(H.hdr64) && f(H.mom64) && f(H.lhdr) && f(H.lmom) &&
            f(H.lhdr64) && f(H.lmom64) && f(H.x0) && f(H.r) && f(H.mom_c) && f(H.leaf_prim) && f(H.leaf_param) &&
            f(H.leaf2) && f(H.leaf2_64) && f(H.leaf3) && f(H.net3) && f(H.net3_64) && f(H.c3) && f(H.c3pts) &&
-           f(H.c3pts64) && f(H.c3n) && f(H.c2) && f(H.c2_64) && f(H.c2mult);
+           f(H.c3pts64) && f(H.c3n) && f(H.c3n64) && f(H.c2) && f(H.c2_64) && f(H.c2mult);
 }
 }  // namespace
 

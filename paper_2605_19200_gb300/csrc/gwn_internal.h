@@ -92,6 +92,14 @@ struct Curve3Info {
 // panels stop at level 0 or 1 evaluates the line integral from this table
 // alone (leaf3_fast32): no curve evaluation per query.
 constexpr int kC3NodeVec = 19;
+// FP64 node table of one boundary curve for the FP64 repair (8-point
+// Gauss-Legendre rule, absolute coordinates), kC3Node64 doubles:
+//   [0..3]      (len0, len1a, len1b, mult), lengths with the 8-point rule's span factor
+//   [4..51]     level-0 panel: 8 nodes x (x, y, z, dx/dt, dy/dt, dz/dt)
+//   [52..99]    level-1 panel [0, 1/2]
+//   [100..147]  level-1 panel [1/2, 1]
+constexpr int kC3Node64 = 148;
+
 // FP32 flops of one node read from a table (fast_panel in kernels3d.cuh): 3
 // subtractions and 31 multiply/add operations, plus a square root and a
 // reciprocal on the special-function unit
@@ -128,6 +136,7 @@ struct DevTree {
     const float4* c3pts;
     const double* c3pts64;     // 4 per point
     const float4* c3n;         // kC3NodeVec per boundary curve
+    const double* c3n64;       // kC3Node64 per boundary curve
     const float4* c2;          // kC2Vec per local curve
     const double* c2_64;       // 12 per local curve
     const float* c2mult;
@@ -179,6 +188,8 @@ struct RepairList {
     uint32_t* rst;      // status bits per entry (3D)
     int2* pairs;        // FP64 (entry, leaf) pairs (3D), kRepairPairCap
     int* npairs;        // their count
+    int2* pairs2;       // those the FP64 node tables left to the full evaluator, kRepairPairCap
+    int* npairs2;       // their count
 };
 
 // Scratch of one in-flight query (one chunk of points), carved from one
@@ -186,6 +197,7 @@ struct RepairList {
 struct Workspace {
     int2* pairs64;    // near-band pairs (capacity n)
     int2* rpairs;     // FP64 repair pairs (kRepairPairCap, 3D)
+    int2* rpairs2;    // of which the full FP64 evaluator takes (kRepairPairCap, 3D)
     double* rw;       // FP64 repair accumulators (n)
     int* perm;        // n
     int* key;         // n: Morton cell of each point (binning)
@@ -197,7 +209,7 @@ struct Workspace {
     int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
                       // [5] overflowed points of the current round (list input), [6] total overflow,
                       // [7] pairs of finished rounds, [8] pairs left to the full evaluator this round,
-                      // [9] the same over finished rounds
+                      // [9] the same over finished rounds, [10] repair pairs the FP64 tables left
     int* olist;       // n: points whose pairs did not fit (rounds alternate with olist2)
     int* olist2;      // n
     unsigned long long* work;  // kWorkCount counters
@@ -205,7 +217,8 @@ struct Workspace {
     int* rlist;       // n: points of this chunk to repair that did not fit the query's list
     int* rlist_g;     // n: the query's points to repair (indices into the whole query), one pass after its last chunk
     uint32_t* rst;    // n: status bits per repair-list entry
-    int* gcount;      // [0] entries of rlist_g, [1] FP64 pairs of its pass (cleared once per query)
+    int* gcount;      // [0] entries of rlist_g, [1] FP64 pairs of its pass, [2] of which the full evaluator
+                      // takes (cleared once per query)
     int rcap;         // entries of rlist_g (= the points a workspace holds)
     long long pair_cap;
 };

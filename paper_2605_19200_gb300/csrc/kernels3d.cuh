@@ -656,6 +656,117 @@ GWN_HD inline float leaf3_eval32(const DevTree& t, int li, float qx, float qy, f
     return (float)leaf3_eval64(t, li, (double)qx, (double)qy, (double)qz, st, kRatio64Band);
 }
 
+// ---- FP64 exact leaf from the FP64 node tables (the repair's far pairs).
+// q (absolute) outside the sphere of radius 1.1 x the leaf's half diagonal:
+// the string points from q away from the leaf (no crossing), and every curve
+// whose 8-point panels stop at level 0 or 1 at panel ratio `ratio` is read from
+// its table.  Same rule and node positions as leaf3_core<double>'s first two
+// levels.  node64 adds one node: weight x A_s(x - q) . x' and the panel test's
+// distance measure min(|r|^2, 2 |r| (|r| + s.r)).
+GWN_HD inline void node64(const double* n, const double q[3], const double s[3], double wk, double& f, double& dm) {
+    const double r0 = n[0] - q[0], r1 = n[1] - q[1], r2 = n[2] - q[2];
+    const double rr = r0 * r0 + r1 * r1 + r2 * r2;
+    const double rn = sqrt(rr);
+    const double sr = s[0] * r0 + s[1] * r1 + s[2] * r2;
+    const double c0 = s[1] * r2 - s[2] * r1, c1 = s[2] * r0 - s[0] * r2, c2 = s[0] * r1 - s[1] * r0;
+    const double den = rn * (rn + sr);
+    f += wk * (c0 * n[3] + c1 * n[4] + c2 * n[5]) / den;
+    dm = fmin(dm, fmin(rr, 2.0 * den));
+}
+
+// the string direction of a far pair: from q towards the leaf centre, unit in FP64
+GWN_HD inline double far_string64(const Leaf3Info& I, const double q[3], double s[3]) {
+    const double dq[3] = {q[0] - (double)I.cen[0], q[1] - (double)I.cen[1], q[2] - (double)I.cen[2]};
+    const double d2 = dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2];
+    const double l = 1.0 / sqrt(d2);
+    s[0] = -dq[0] * l;
+    s[1] = -dq[1] * l;
+    s[2] = -dq[2] * l;
+    return d2;
+}
+
+// one thread (host execution and tests); false where leaf3_core<double> is needed
+GWN_HD inline bool leaf3_fast64(const DevTree& t, int li, const double q[3], double ratio, double* out) {
+    const Leaf3Info I = t.leaf3[li];
+    double s[3];
+    const double d2 = far_string64(I, q, s);
+    const double rfar = 1.1 * (double)I.rad;
+    if (!t.c3n64 || !(d2 > rfar * rfar)) return false;
+    const double ratio2 = ratio * ratio;
+    double acc = 0;
+    for (int c = 0; c < I.c3_cnt; ++c) {
+        const double* H = t.c3n64 + (size_t)(I.c3_off + c) * kC3Node64;
+        double f = 0, dm = 1e300;
+        for (int k = 0; k < 8; ++k) node64(H + 4 + 6 * k, q, s, GWN_GLW(k), f, dm);
+        if (H[0] * H[0] <= ratio2 * dm) {
+            acc += H[3] * f;
+            continue;
+        }
+        double fa = 0, da = 1e300, fb = 0, db = 1e300;
+        for (int k = 0; k < 8; ++k) {
+            node64(H + 52 + 6 * k, q, s, GWN_GLW(k), fa, da);
+            node64(H + 100 + 6 * k, q, s, GWN_GLW(k), fb, db);
+        }
+        if (H[1] * H[1] > ratio2 * da || H[2] * H[2] > ratio2 * db) return false;
+        acc += H[3] * 0.5 * (fa + fb);
+    }
+    *out = acc * 0.07957747154594767;  // 1 / (4 pi)
+    return true;
+}
+
+#if defined(__CUDACC__)
+// the same spread over a warp: 4 curves at a time, 8 lanes per curve (one
+// node each), panel sums and distance measures reduced within the 8 lanes
+__device__ inline bool leaf3_fast64_warp(const DevTree& t, int li, const double q[3], double ratio, double* out) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, grp = lane >> 3, k = lane & 7;
+    const Leaf3Info I = t.leaf3[li];
+    double s[3];
+    const double d2 = far_string64(I, q, s);
+    const double rfar = 1.1 * (double)I.rad;
+    if (!t.c3n64 || !(d2 > rfar * rfar)) return false;
+    const double ratio2 = ratio * ratio;
+    const double wk = GWN_GLW(k);
+    double acc = 0;
+    bool deep = false;
+    for (int c0 = 0; c0 < I.c3_cnt; c0 += 4) {
+        const int c = c0 + grp;
+        const bool act = c < I.c3_cnt;
+        const double* H = t.c3n64 + (size_t)(I.c3_off + (act ? c : 0)) * kC3Node64;
+        double f = 0, dm = 1e300;
+        if (act) node64(H + 4 + 6 * k, q, s, wk, f, dm);
+        for (int off = 1; off < 8; off <<= 1) {
+            f += __shfl_xor_sync(full, f, off);
+            dm = fmin(dm, __shfl_xor_sync(full, dm, off));
+        }
+        const bool need1 = act && H[0] * H[0] > ratio2 * dm;
+        double val = f;
+        if (__any_sync(full, need1)) {
+            double fa = 0, da = 1e300, fb = 0, db = 1e300;
+            if (need1) {
+                node64(H + 52 + 6 * k, q, s, wk, fa, da);
+                node64(H + 100 + 6 * k, q, s, wk, fb, db);
+            }
+            for (int off = 1; off < 8; off <<= 1) {
+                fa += __shfl_xor_sync(full, fa, off);
+                fb += __shfl_xor_sync(full, fb, off);
+                da = fmin(da, __shfl_xor_sync(full, da, off));
+                db = fmin(db, __shfl_xor_sync(full, db, off));
+            }
+            if (need1) {
+                if (H[1] * H[1] > ratio2 * da || H[2] * H[2] > ratio2 * db) deep = true;
+                val = 0.5 * (fa + fb);
+            }
+        }
+        if (act && k == 0) acc += H[3] * val;
+    }
+    if (__any_sync(full, deep)) return false;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(full, acc, off);
+    *out = acc * 0.07957747154594767;  // 1 / (4 pi)
+    return true;
+}
+#endif
+
 // ---- One FP64 leaf evaluation spread over a warp (near band and repair).
 // In one thread, an evaluation close to a boundary curve runs hundreds of
 // Gauss-Legendre nodes one after another at FP64 latency, and such a single

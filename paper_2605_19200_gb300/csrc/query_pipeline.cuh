@@ -495,13 +495,43 @@ __global__ void k_finish(int n, const float* wacc, const uint32_t* stv, int prec
 
 namespace gwn {
 
-// FP64 repair pairs with one warp per pair (leaf3_warp64)
-__global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts, int dtype, RepairList R) {
-    __shared__ int2 sstk[4][kQuadStack];
+__device__ __forceinline__ void load_point_d(const void* pts, int dtype, long long i, double q[3]) {
+    if (dtype == GWN_F32) {
+        const float* p = reinterpret_cast<const float*>(pts) + (size_t)i * 3;
+        q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+    } else {
+        const double* p = reinterpret_cast<const double*>(pts) + (size_t)i * 3;
+        q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+    }
+}
+
+// FP64 repair pairs from the FP64 node tables, one warp per pair
+// (leaf3_fast64_warp: far pairs whose 8-point panels stop at level 0 or 1, at
+// the repair ratio); the others go to the second list for k_rpairs3_warp
+__global__ void __launch_bounds__(128) k_rpairs3_fast(DevTree t, const void* pts, int dtype, RepairList R) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long np = min((long long)*R.npairs, kRepairPairCap);
     for (long long j = (long long)blockIdx.x * 4 + wid; j < np; j += (long long)gridDim.x * 4) {
         const int2 pr = R.pairs[j];
+        double q[3];
+        load_point_d(pts, dtype, R.idx[pr.x], q);
+        double v = 0;
+        const bool ok = leaf3_fast64_warp(t, pr.y, q, kRatio64Repair, &v);
+        if (lane == 0) {
+            if (ok) atomicAdd(&R.rw[pr.x], v);
+            else R.pairs2[atomicAdd(R.npairs2, 1)] = pr;
+        }
+        __syncwarp();
+    }
+}
+
+// FP64 repair pairs with one warp per pair (leaf3_warp64): those the tables left
+__global__ void __launch_bounds__(128) k_rpairs3_warp(DevTree t, const void* pts, int dtype, RepairList R) {
+    __shared__ int2 sstk[4][kQuadStack];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long np = min((long long)*R.npairs2, kRepairPairCap);
+    for (long long j = (long long)blockIdx.x * 4 + wid; j < np; j += (long long)gridDim.x * 4) {
+        const int2 pr = R.pairs2[j];
         const int qi = R.idx[pr.x];
         double q[3];
         if (dtype == GWN_F32) {

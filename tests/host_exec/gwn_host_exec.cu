@@ -76,6 +76,7 @@ DevTree host_tree(const HostModel& H, int leaf_far) {
     t.c3pts = H.c3pts.data();
     t.c3pts64 = H.c3pts64.data();
     t.c3n = H.c3n.empty() ? nullptr : H.c3n.data();
+    t.c3n64 = H.c3n64.empty() ? nullptr : H.c3n64.data();
     t.c2 = H.c2.data();
     t.c2_64 = H.c2_64.data();
     t.c2mult = H.c2mult.data();
@@ -169,6 +170,28 @@ extern "C" int hx_leaf_paths3(const gwn_patch3d* patches, size_t n, const gwn_bu
             full32[k] = leaf3_try32(t, l, qf[0], qf[1], qf[2], &v, nullptr, false) ? (double)v : NAN;
             uint32_t st = 0;
             exact64[k] = leaf3_eval64(t, l, (double)qf[0], (double)qf[1], (double)qf[2], st);
+        }
+    return t.n_leaves;
+}
+
+// Per (query, leaf) pair: the FP64 value from the FP64 node tables at the
+// repair's panel ratio (fast64, NaN where leaf3_fast64 declines) and the full
+// FP64 evaluation (exact64).  Arrays hold nq x n_leaves values.
+extern "C" int hx_leaf_paths64(const gwn_patch3d* patches, size_t n, const gwn_build_opts* o, const double* q, int nq,
+                               double* fast64, double* exact64, int max_leaves) {
+    init_tables();
+    HostModel H;
+    gwn_status code;
+    if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
+    const DevTree t = host_tree(H, 1);
+    if (t.n_leaves > max_leaves) return -2;
+    for (int i = 0; i < nq; ++i)
+        for (int l = 0; l < t.n_leaves; ++l) {
+            const size_t k = (size_t)i * t.n_leaves + l;
+            double v = 0;
+            fast64[k] = leaf3_fast64(t, l, q + 3 * i, kRatio64Repair, &v) ? v : NAN;
+            uint32_t st = 0;
+            exact64[k] = leaf3_eval64(t, l, q[3 * i], q[3 * i + 1], q[3 * i + 2], st);
         }
     return t.n_leaves;
 }

@@ -47,6 +47,8 @@ def hx():
                               ctypes.c_double, P, P, P, P, P]
     lib.hx_leaf_paths3.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), P, ctypes.c_int,
                                    P, P, P, ctypes.c_int]
+    lib.hx_leaf_paths64.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), P, ctypes.c_int,
+                                    P, P, ctypes.c_int]
     return lib
 
 
@@ -354,3 +356,28 @@ def test_node_tables_match_the_full_evaluation(hx, shape):
     both = took & np.isfinite(full)
     assert np.max(np.abs(fast[both] - full[both])) <= 2e-6
     assert np.max(np.abs(fast[took] - ex[took])) <= 2e-6
+
+
+@pytest.mark.parametrize("shape", ["cad", "sphere"])
+def test_fp64_node_tables_match_the_full_evaluation(hx, shape):
+    """The FP64 repair reads far (point, leaf) pairs from FP64 node tables
+    (8-point rule, levels 0 and 1): per pair it must agree with the full FP64
+    evaluation to FP64 quadrature accuracy, and take most far pairs."""
+    if shape == "cad":
+        patches, q = configs.cad_3d(1234, 120, 60)
+    else:
+        patches, q = configs.sphere_3d(n_queries=60)
+    parr, keep = api.marshal_patches(patches)
+    o = api.default_build_opts(beta=6.0, beta_leaf=4.0)
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    nmax = 4096
+    fast, ex = np.zeros(qq.shape[0] * nmax), np.zeros(qq.shape[0] * nmax)
+    nl = hx.hx_leaf_paths64(ctypes.cast(parr, ctypes.c_void_p), len(patches), ctypes.byref(o), qq.ctypes.data,
+                            qq.shape[0], fast.ctypes.data, ex.ctypes.data, nmax)
+    assert nl > 0
+    fast, ex = fast[:qq.shape[0] * nl], ex[:qq.shape[0] * nl]
+    took = np.isfinite(fast)
+    assert took.mean() > 0.8
+    # the reference integrates at panel ratio 0.5, the repair's tables at 1.0 (the
+    # repair's own 8-point ratio): they differ by the coarser rule's ~1e-9
+    assert np.max(np.abs(fast[took] - ex[took])) <= 5e-9

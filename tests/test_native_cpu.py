@@ -249,7 +249,7 @@ def test_model_load_rejects_bad_files(tmp_path):
 _ARRAY_ELEM = [("child", 8), ("hdr", 16), ("mom", 16), ("hdr64", 8), ("mom64", 8), ("lhdr", 16), ("lmom", 16),
                ("lhdr64", 8), ("lmom64", 8), ("x0", 8), ("r", 8), ("mom_c", 8), ("leaf_prim", 8),
                ("leaf_param", 8), ("leaf2", 16), ("leaf2_64", 8), ("leaf3", 48), ("net3", 16), ("net3_64", 8),
-               ("c3", 16), ("c3pts", 16), ("c3pts64", 8), ("c3n", 16), ("c2", 16), ("c2_64", 8), ("c2mult", 4)]
+               ("c3", 16), ("c3pts", 16), ("c3pts64", 8), ("c3n", 16), ("c3n64", 8), ("c2", 16), ("c2_64", 8), ("c2mult", 4)]
 
 
 def _split_model_file(data):

@@ -371,7 +371,7 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     const long long cap = dim != 2 ? (long long)n * 96 + 65536 : 0;
     const size_t cells2 = (size_t)1 << (2 * kBinBits2), cells3 = (size_t)1 << (3 * kBinBits3);
     const size_t cells = dim == 2 ? cells2 : dim == 3 ? cells3 : std::max(cells2, cells3);
-    const size_t hist = cells + 1;
+    const size_t hist = std::max(cells, (size_t)n_leaves) + 1;
     const size_t keyn = n;
     size_t off = 0;
     auto carve = [&](size_t bytes) {
@@ -582,14 +582,19 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
                                           round == 0 ? nullptr : ws.counters + 5, olist_out);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
                 GWN_CUDA_TRY(cudaGetLastError());
-                // 3. exact leaves (the list comes in runs of one leaf): far pairs from
-                // the node tables; the rest, in list order, to the full evaluator
+                // 3. exact leaves, sorted by leaf (one atomic per run of a leaf); far
+                // pairs from the node tables, the rest, in leaf order, to the full
+                // evaluator (ws.pairs is free again once the sorted copy exists)
+                GWN_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, (size_t)m->host.n_leaves * sizeof(int), st));
+                k_pair_hist<<<(unsigned)(sms * 16), B, 0, st>>>(ws.pair_cap, ws.counters, ws.pairs, ws.hist);
+                k_scan<<<1, 1024, 0, st>>>(ws.hist, m->host.n_leaves);
+                k_pair_sort<<<(unsigned)(sms * 16), B, 0, st>>>(ws.pair_cap, ws.counters, ws.pairs, ws.hist, ws.pairs2);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[2], st));
                 k_pair_fast<<<(unsigned)(sms * 16), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters,
-                                                                ws.pairs, ws.wacc, ws.st, ws.pairs2, p.work);
+                                                                ws.pairs2, ws.wacc, ws.st, ws.pairs, p.work);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[4], st));
                 k_pair_eval<<<(unsigned)(sms * 8), B, 0, st>>>(m->tree, pts, dtype, ws.pair_cap, ws.counters + 8,
-                                                               ws.counters, ws.pairs2, ws.wacc, ws.st, ws.pairs64, ni,
+                                                               ws.counters, ws.pairs, ws.wacc, ws.st, ws.pairs64, ni,
                                                                p.work);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[3], st));
                 if (round < 2) k_next_round<<<1, 32, 0, st>>>(ws);

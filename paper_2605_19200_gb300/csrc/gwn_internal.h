@@ -201,11 +201,12 @@ struct Workspace {
     double* rw;       // FP64 repair accumulators (n)
     int* perm;        // n
     int* key;         // n: Morton cell of each point (binning)
-    int* hist;        // cells + 1
+    int* hist;        // max(cells, n_leaves) + 1: binning histogram, then the pair sort's
     float* wacc;      // n
     uint32_t* st;     // n
-    int2* pairs;      // pair capacity: (point, leaf) pairs of the traversal, in runs of one leaf
-    int2* pairs2;     // pair capacity: those left to the full evaluator
+    int2* pairs;      // pair capacity: (point, leaf) pairs of the traversal, in runs of one leaf;
+                      // then those the node tables left to the full evaluator
+    int2* pairs2;     // pair capacity: the pairs sorted by leaf
     int* counters;    // [0] pairs, [1] repair count, [2] near-band pairs, [3] overflowed points, [4] repair pairs,
                       // [5] overflowed points of the current round (list input), [6] total overflow,
                       // [7] pairs of finished rounds, [8] pairs left to the full evaluator this round,

@@ -12,10 +12,10 @@
 //     shared-memory buffer, one atomic per 128 pairs;
 //     points whose pairs do not fit are traversed again in up to two more
 //     rounds.
-//  3. 3D only: one thread per pair evaluates the leaf in FP32 and adds it to
-//     the point's accumulator.  The traversal writes each leaf's pairs in one
-//     run, so consecutive threads share the leaf and a warp reads one or two
-//     sets of boundary curves.  Far pairs whose panels stop at level 0 or 1 (nearly
+//  3. 3D only: the work list is counting-sorted by leaf (one atomic per run of
+//     a leaf, as the traversal writes them), and one thread per pair evaluates
+//     the leaf in FP32 and adds it to the point's accumulator.  Consecutive
+//     threads share the leaf, so a warp reads one set of boundary curves.  Far pairs whose panels stop at level 0 or 1 (nearly
 //     all) read the curves' query-independent node tables (k_pair_fast); the
 //     rest take the full evaluation (k_pair_eval: foot-point search, adaptive
 //     panels from the Bernstein form).  Pairs FP32 cannot resolve go to the
@@ -278,9 +278,44 @@ __global__ void __launch_bounds__(128) k_overflow3(DevTree t, const void* pts, i
     }
 }
 
+// Counting sort of the pair list by leaf, one run at a time: the traversal
+// writes each leaf's pairs of a warp in one run, so the lanes of a warp that
+// hold the same leaf (__match_any_sync) take one atomic for their run, in the
+// histogram pass and in the scatter pass.  Sorted, a leaf's pairs from every
+// warp are contiguous and the pair kernels read its tables once for many warps.
+__global__ void k_pair_hist(long long npair_cap, const int* counters, const int2* pairs, int* hist) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long np = min((long long)counters[0], npair_cap);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long k = base + threadIdx.x;
+        const int leaf = k < np ? pairs[k].y : -1;
+        const unsigned m = __match_any_sync(full, leaf);
+        if (leaf >= 0 && lane == __ffs(m) - 1) atomicAdd(&hist[leaf], __popc(m));
+    }
+}
+
+__global__ void k_pair_sort(long long npair_cap, const int* counters, const int2* pairs, int* cursor, int2* out) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long np = min((long long)counters[0], npair_cap);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long k = base + threadIdx.x;
+        const int2 pr = k < np ? pairs[k] : make_int2(0, -1);
+        const unsigned m = __match_any_sync(full, pr.y);
+        const int leader = __ffs(m) - 1;
+        int start = 0;
+        if (pr.y >= 0 && lane == leader) start = atomicAdd(&cursor[pr.y], __popc(m));
+        start = __shfl_sync(full, start, leader);
+        if (pr.y >= 0) out[start + __popc(m & ((1u << lane) - 1u))] = pr;
+    }
+}
+
 // exact 3D leaves from the node tables, one thread per (point, leaf) pair in
-// list order (runs of one leaf, so the 32 pairs of a warp mostly share one or
-// two leaves and their tables are read once for the warp): pairs whose point lies outside the leaf's
+// leaf order (the 32 pairs of a warp mostly share one leaf, so its table is
+// read once for the warp, and consecutive warps reuse it from L1): pairs whose point lies outside the leaf's
 // 1.1-radius sphere and whose panels stop at level 0 or 1 add their value
 // here (leaf3_fast32).  The others -- points near the leaf, whose string needs
 // the foot-point search, and curves that need deeper panels -- are appended in

@@ -733,6 +733,88 @@ std::string validate_curve(const gwn_curve2d& C, double U0, double U1, double V0
 
 }  // namespace
 
+// The boundary data of one leaf (curves composed with its net, their point
+// copies, node tables and local 2D curves), packed on its own so that leaves
+// are packed in parallel; ctrl_off counts from the leaf's first curve point.
+struct LeafPack {
+    std::vector<Curve3Info> c3;
+    std::vector<float4> c3pts;
+    std::vector<double> c3pts64;
+    std::vector<float4> c3n;
+    std::vector<double> c3n64;
+    std::vector<float4> c2;
+    std::vector<double> c2_64;
+    std::vector<float> c2mult;
+};
+
+void pack_leaf(const Leaf& L, const float cen[3], const std::vector<double>& g4x, const std::vector<double>& g4w,
+               const std::vector<double>& g8x, LeafPack* P) {
+    std::vector<double> X;
+    for (size_t b = 0; b < L.bnd.size(); ++b) {
+        compose(L.bnd[b], L.net, &X);
+        int D = 6 * L.bnd[b].deg;
+        Curve3Info ci;
+        ci.ctrl_off = (int32_t)P->c3pts.size();
+        ci.deg = D;
+        ci.mult = (float)L.mult[b];
+        ci.min_level = curve_min_level(X, D, g4x, g4w);
+        P->c3.push_back(ci);
+        {
+            float4 tab[kC3NodeVec];
+            node_table(X, D, cen, ci.mult, g4x, tab);
+            P->c3n.insert(P->c3n.end(), tab, tab + kC3NodeVec);
+            double tab64[kC3Node64];
+            node_table64(X, D, (double)L.mult[b], g8x, tab64);
+            P->c3n64.insert(P->c3n64.end(), tab64, tab64 + kC3Node64);
+        }
+        // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i),
+        // then the same 2 D + 1 points of the reversed curve (evaluation for t > 1/2);
+        // float copies relative to the leaf centre, double copies absolute
+        std::vector<double> rel((size_t)(D + 1) * 4);
+        for (int t = 0; t <= D; ++t) {
+            const double* h = &X[(size_t)t * 4];
+            double r4[4] = {h[0] - cen[0] * h[3], h[1] - cen[1] * h[3], h[2] - cen[2] * h[3], h[3]};
+            for (int k = 0; k < 4; ++k) rel[(size_t)t * 4 + k] = r4[k];
+            double c = binom(D, t);
+            P->c3pts.push_back(float4{(float)(c * r4[0]), (float)(c * r4[1]), (float)(c * r4[2]), (float)(c * r4[3])});
+            for (int k = 0; k < 4; ++k) P->c3pts64.push_back(c * h[k]);
+        }
+        for (int t = 0; t < D; ++t) {
+            double c = binom(D - 1, t);
+            float f[4];
+            for (int k = 0; k < 4; ++k) {
+                f[k] = (float)(c * (rel[(size_t)(t + 1) * 4 + k] - rel[(size_t)t * 4 + k]));
+                P->c3pts64.push_back(c * (X[(size_t)(t + 1) * 4 + k] - X[(size_t)t * 4 + k]));
+            }
+            P->c3pts.push_back(float4{f[0], f[1], f[2], f[3]});
+        }
+        {
+            // reversed copy: R_i = P_{D-i}, RQ_i = Q_{D-1-i}
+            const size_t f0 = (size_t)ci.ctrl_off, d0 = (size_t)ci.ctrl_off * 4;
+            for (int t = 0; t <= D; ++t) {
+                P->c3pts.push_back(P->c3pts[f0 + (size_t)(D - t)]);
+                for (int k = 0; k < 4; ++k) P->c3pts64.push_back(P->c3pts64[d0 + (size_t)(D - t) * 4 + k]);
+            }
+            for (int t = 0; t < D; ++t) {
+                P->c3pts.push_back(P->c3pts[f0 + (size_t)(D + 1 + D - 1 - t)]);
+                for (int k = 0; k < 4; ++k)
+                    P->c3pts64.push_back(P->c3pts64[d0 + (size_t)(D + 1 + D - 1 - t) * 4 + k]);
+            }
+        }
+        TP e3 = tp_elevate3(L.bnd[b]);
+        float f[12];
+        for (int t = 0; t < 4; ++t)
+            for (int k = 0; k < 3; ++k) {
+                f[t * 3 + k] = (float)e3.h[t][k];
+                P->c2_64.push_back(e3.h[t][k]);
+            }
+        P->c2.push_back(float4{f[0], f[1], f[2], f[3]});
+        P->c2.push_back(float4{f[4], f[5], f[6], f[7]});
+        P->c2.push_back(float4{f[8], f[9], f[10], f[11]});
+        P->c2mult.push_back((float)L.mult[b]);
+    }
+}
+
 std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build_opts& o, HostModel* out,
                            gwn_status* code) {
     *code = GWN_ERR_INVALID_ARG;
@@ -903,102 +985,70 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
     out->leaf3.resize(nl);
     out->net3.resize((size_t)nl * kNet3Vec);
     out->net3_64.resize((size_t)nl * 64);
-    std::vector<double> X;
     std::vector<double> g4x, g4w, g8x, g8w;  // the FP32 rule (tables, minimum levels) and the FP64 rule
     gauss_legendre01(4, &g4x, &g4w);
     gauss_legendre01(8, &g8x, &g8w);
-    for (int i = 0; i < nl; ++i) {
-        const Leaf& L = leaves[perm[i]];
-        out->leaf_prim[i] = L.prim;
-        out->leaf_param[i * 4 + 0] = L.R.u0;
-        out->leaf_param[i * 4 + 1] = L.R.u1;
-        out->leaf_param[i * 4 + 2] = L.R.v0;
-        out->leaf_param[i * 4 + 3] = L.R.v1;
-        Leaf3Info I;
-        float cen[3];
-        for (int k = 0; k < 3; ++k) {
-            cen[k] = (float)(0.5 * (L.lo[k] + L.hi[k]));
-            I.cen[k] = cen[k];
-            I.nrm[k] = (float)L.nrm[k];
-        }
-        double dg = dist3(L.lo, L.hi);
-        I.diag = (float)dg;
-        I.rad = (float)(0.5 * dg);
-        for (int a = 0; a < 4; ++a)
-            for (int b = 0; b < 4; ++b) {
-                const double* h = L.net.h[a][b];
-                out->net3[(size_t)i * kNet3Vec + a * 4 + b] =
-                    float4{(float)(h[0] - cen[0] * h[3]), (float)(h[1] - cen[1] * h[3]), (float)(h[2] - cen[2] * h[3]), (float)h[3]};
-                for (int k = 0; k < 4; ++k) out->net3_64[(size_t)i * 64 + (a * 4 + b) * 4 + k] = h[k];
+    // every leaf's boundary data on its own, in parallel over leaves (composing
+    // the curves and tabulating their nodes is most of the build), then the
+    // pieces are concatenated in BVH order
+    std::vector<LeafPack> packs(nl);
+    {
+        std::atomic<int> next_leaf{0};
+        auto pack_worker = [&]() {
+            for (int i; (i = next_leaf.fetch_add(1)) < nl;) {
+                const Leaf& L = leaves[perm[i]];
+                out->leaf_prim[i] = L.prim;
+                out->leaf_param[i * 4 + 0] = L.R.u0;
+                out->leaf_param[i * 4 + 1] = L.R.u1;
+                out->leaf_param[i * 4 + 2] = L.R.v0;
+                out->leaf_param[i * 4 + 3] = L.R.v1;
+                Leaf3Info I;
+                float cen[3];
+                for (int k = 0; k < 3; ++k) {
+                    cen[k] = (float)(0.5 * (L.lo[k] + L.hi[k]));
+                    I.cen[k] = cen[k];
+                    I.nrm[k] = (float)L.nrm[k];
+                }
+                double dg = dist3(L.lo, L.hi);
+                I.diag = (float)dg;
+                I.rad = (float)(0.5 * dg);
+                for (int a = 0; a < 4; ++a)
+                    for (int b = 0; b < 4; ++b) {
+                        const double* h = L.net.h[a][b];
+                        out->net3[(size_t)i * kNet3Vec + a * 4 + b] =
+                            float4{(float)(h[0] - cen[0] * h[3]), (float)(h[1] - cen[1] * h[3]),
+                                   (float)(h[2] - cen[2] * h[3]), (float)h[3]};
+                        for (int k = 0; k < 4; ++k) out->net3_64[(size_t)i * 64 + (a * 4 + b) * 4 + k] = h[k];
+                    }
+                I.c3_cnt = (int32_t)L.bnd.size();
+                I.c2_cnt = (int32_t)L.bnd.size();
+                out->leaf3[i] = I;  // offsets follow when the pieces are concatenated
+                pack_leaf(L, cen, g4x, g4w, g8x, &packs[i]);
             }
+        };
+        std::vector<std::thread> pth;
+        for (int t = 1; t < nt; ++t) pth.emplace_back(pack_worker);
+        pack_worker();
+        for (auto& t : pth) t.join();
+    }
+    for (int i = 0; i < nl; ++i) {
+        LeafPack& P = packs[i];
+        Leaf3Info& I = out->leaf3[i];
         I.c3_off = (int32_t)out->c3.size();
         I.c2_off = (int32_t)(out->c2.size() / kC2Vec);
-        for (size_t b = 0; b < L.bnd.size(); ++b) {
-            compose(L.bnd[b], L.net, &X);
-            int D = 6 * L.bnd[b].deg;
-            Curve3Info ci;
-            ci.ctrl_off = (int32_t)out->c3pts.size();
-            ci.deg = D;
-            ci.mult = (float)L.mult[b];
-            ci.min_level = curve_min_level(X, D, g4x, g4w);
+        const int32_t base = (int32_t)out->c3pts.size();
+        for (Curve3Info ci : P.c3) {
+            ci.ctrl_off += base;
             out->c3.push_back(ci);
-            {
-                float4 tab[kC3NodeVec];
-                node_table(X, D, cen, ci.mult, g4x, tab);
-                out->c3n.insert(out->c3n.end(), tab, tab + kC3NodeVec);
-                double tab64[kC3Node64];
-                node_table64(X, D, (double)L.mult[b], g8x, tab64);
-                out->c3n64.insert(out->c3n64.end(), tab64, tab64 + kC3Node64);
-            }
-            // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i),
-            // then the same 2 D + 1 points of the reversed curve (evaluation for t > 1/2);
-            // float copies relative to the leaf centre, double copies absolute
-            std::vector<double> rel((size_t)(D + 1) * 4);
-            for (int t = 0; t <= D; ++t) {
-                const double* h = &X[(size_t)t * 4];
-                double r4[4] = {h[0] - cen[0] * h[3], h[1] - cen[1] * h[3], h[2] - cen[2] * h[3], h[3]};
-                for (int k = 0; k < 4; ++k) rel[(size_t)t * 4 + k] = r4[k];
-                double c = binom(D, t);
-                out->c3pts.push_back(float4{(float)(c * r4[0]), (float)(c * r4[1]), (float)(c * r4[2]), (float)(c * r4[3])});
-                for (int k = 0; k < 4; ++k) out->c3pts64.push_back(c * h[k]);
-            }
-            for (int t = 0; t < D; ++t) {
-                double c = binom(D - 1, t);
-                float f[4];
-                for (int k = 0; k < 4; ++k) {
-                    f[k] = (float)(c * (rel[(size_t)(t + 1) * 4 + k] - rel[(size_t)t * 4 + k]));
-                    out->c3pts64.push_back(c * (X[(size_t)(t + 1) * 4 + k] - X[(size_t)t * 4 + k]));
-                }
-                out->c3pts.push_back(float4{f[0], f[1], f[2], f[3]});
-            }
-            {
-                // reversed copy: R_i = P_{D-i}, RQ_i = Q_{D-1-i}
-                const size_t f0 = (size_t)ci.ctrl_off, d0 = (size_t)ci.ctrl_off * 4;
-                for (int t = 0; t <= D; ++t) {
-                    out->c3pts.push_back(out->c3pts[f0 + (size_t)(D - t)]);
-                    for (int k = 0; k < 4; ++k) out->c3pts64.push_back(out->c3pts64[d0 + (size_t)(D - t) * 4 + k]);
-                }
-                for (int t = 0; t < D; ++t) {
-                    out->c3pts.push_back(out->c3pts[f0 + (size_t)(D + 1 + D - 1 - t)]);
-                    for (int k = 0; k < 4; ++k)
-                        out->c3pts64.push_back(out->c3pts64[d0 + (size_t)(D + 1 + D - 1 - t) * 4 + k]);
-                }
-            }
-            TP e3 = tp_elevate3(L.bnd[b]);
-            float f[12];
-            for (int t = 0; t < 4; ++t)
-                for (int k = 0; k < 3; ++k) {
-                    f[t * 3 + k] = (float)e3.h[t][k];
-                    out->c2_64.push_back(e3.h[t][k]);
-                }
-            out->c2.push_back(float4{f[0], f[1], f[2], f[3]});
-            out->c2.push_back(float4{f[4], f[5], f[6], f[7]});
-            out->c2.push_back(float4{f[8], f[9], f[10], f[11]});
-            out->c2mult.push_back((float)L.mult[b]);
         }
-        I.c3_cnt = (int32_t)L.bnd.size();
-        I.c2_cnt = (int32_t)L.bnd.size();
-        out->leaf3[i] = I;
+        out->c3pts.insert(out->c3pts.end(), P.c3pts.begin(), P.c3pts.end());
+        out->c3pts64.insert(out->c3pts64.end(), P.c3pts64.begin(), P.c3pts64.end());
+        out->c3n.insert(out->c3n.end(), P.c3n.begin(), P.c3n.end());
+        out->c3n64.insert(out->c3n64.end(), P.c3n64.begin(), P.c3n64.end());
+        out->c2.insert(out->c2.end(), P.c2.begin(), P.c2.end());
+        out->c2_64.insert(out->c2_64.end(), P.c2_64.begin(), P.c2_64.end());
+        out->c2mult.insert(out->c2mult.end(), P.c2mult.begin(), P.c2mult.end());
+        P = LeafPack();  // release as we go
     }
     *code = GWN_OK;
     return "";

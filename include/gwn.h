@@ -101,8 +101,11 @@ typedef struct {
     double tolerance;     /* target max |dGWN| for the FP32 path (default 1e-4) */
     double max_aabb_frac; /* subdivide until a leaf's box diagonal < frac * shape diagonal (0.1); <= 0: no subdivision */
     int32_t order;        /* Taylor order 0, 1 or 2 (default 2) */
-    double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2, or 0 = choose
-                             beta (and beta_leaf) by the autotuner to meet `tolerance` (default 2) */
+    double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2, or 0 = autotune:
+                             among the (beta, beta_leaf) pairs whose FP32 error on validation points
+                             (FP64 direct sum on the device) stays below tolerance / 2, the fastest on
+                             a timed uniform sample, then the binning resolution by measured time
+                             (default 2) */
     double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves;
                              < 0 = automatic: direct sum up to 512 leaves, else 3 x beta (default -1) */
     double repair_band;   /* re-evaluate in FP64 when |w - round(w) +- 1/2| < band (default 1e-3) */
@@ -209,6 +212,9 @@ typedef struct {
     double lo[3], hi[3];    /* box of all control points */
     double beta_leaf;       /* far-test factor of the leaves (3D; equals beta unless set or tuned) */
     int32_t device;         /* CUDA ordinal holding the model, or GWN_DEVICE_HOST_ONLY */
+    int32_t bin_bits;       /* Morton-cell bits per axis of the query's spatial binning (3D: picked by
+                               the autotuner from 4..6 by measured time; 2D: 9) */
+    int32_t stack_depth;    /* warp-stack entries of the packet traversal (from the tree depth) */
 } gwn_model_stats;
 
 gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);

@@ -64,7 +64,8 @@ class gwn_model_stats(ctypes.Structure):
                 ("n_nodes", ctypes.c_int64), ("max_depth", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("build_ms", ctypes.c_double), ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double),
                 ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double), ("device", ctypes.c_int32)]
+                ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double), ("device", ctypes.c_int32),
+                ("bin_bits", ctypes.c_int32), ("stack_depth", ctypes.c_int32)]
 
 
 class gwn_serve_opts(ctypes.Structure):

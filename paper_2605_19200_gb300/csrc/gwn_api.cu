@@ -21,6 +21,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <sys/stat.h>
@@ -206,6 +207,11 @@ gwn_status upload_model(gwn_model_s* m) {
 }
 
 gwn_status finish_build(gwn_model_s* m, gwn_model* out) {
+    // the packet traversal's warp stack holds the pending second children along
+    // one root-to-leaf path: sized from the tree's depth (deeper paths overflow,
+    // are flagged and repaired)
+    const int need = m->host.max_depth + 8;
+    m->stack_depth = need <= 64 ? 64 : need <= 96 ? 96 : 128;
     gwn_status s = upload_model(m);
     if (s != GWN_OK) {
         free_model_memory(m);
@@ -369,8 +375,7 @@ __global__ void __launch_bounds__(128) k_repair(DevTree t, const void* pts, int 
 // dim 0 lays out a workspace that serves both 2D and 3D models.
 size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* ws) {
     const long long cap = dim != 2 ? (long long)n * 96 + 65536 : 0;
-    const size_t cells2 = (size_t)1 << (2 * kBinBits2), cells3 = (size_t)1 << (3 * kBinBits3);
-    const size_t cells = dim == 2 ? cells2 : dim == 3 ? cells3 : std::max(cells2, cells3);
+    const size_t cells = kMaxBinCells;  // the finest binning of either dimension
     const size_t hist = std::max(cells, (size_t)n_leaves) + 1;
     const size_t keyn = n;
     size_t off = 0;
@@ -545,7 +550,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         // 1. spatial binning of the points (counting sort by Morton cell)
         const int* perm = nullptr;
         if (n >= 2048) {
-            const int bits = m->dim == 2 ? kBinBits2 : kBinBits3;
+            const int bits = m->dim == 2 ? kBinBits2 : m->bin_bits3;
             const int cells = 1 << (m->dim * bits);
             float3 lo = make_float3((float)m->host.lo[0], (float)m->host.lo[1], (float)m->host.lo[2]);
             float ex[3];
@@ -555,8 +560,8 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
             }
             float3 inv = make_float3(ex[0], ex[1], ex[2]);
             GWN_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, (size_t)cells * sizeof(int), st));
-            if (m->dim == 2) k_bin<2><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, ws.key, ws.hist);
-            else k_bin<3><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, ws.key, ws.hist);
+            if (m->dim == 2) k_bin<2><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, bits, ws.key, ws.hist);
+            else k_bin<3><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, bits, ws.key, ws.hist);
             k_scan<<<1, 1024, 0, st>>>(ws.hist, cells);
             k_scatter_perm<<<nb, B, 0, st>>>(ni, ws.key, ws.hist, ws.perm);
             GWN_CUDA_TRY(cudaGetLastError());
@@ -578,8 +583,16 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
             for (int round = 0; round < 3; ++round) {
                 const int* list = round == 0 ? perm : (round == 1 ? ws.olist : ws.olist2);
                 int* olist_out = round == 1 ? ws.olist2 : ws.olist;
-                k_trav3<<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
-                                          round == 0 ? nullptr : ws.counters + 5, olist_out);
+                const int* ndev = round == 0 ? nullptr : ws.counters + 5;
+                if (m->stack_depth <= 64)
+                    k_trav3<64><<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
+                                                  ndev, olist_out);
+                else if (m->stack_depth <= 96)
+                    k_trav3<96><<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
+                                                  ndev, olist_out);
+                else
+                    k_trav3<128><<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
+                                                   ndev, olist_out);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
                 GWN_CUDA_TRY(cudaGetLastError());
                 // 3. exact leaves, sorted by leaf (one atomic per run of a leaf); far
@@ -753,6 +766,7 @@ static gwn_status autotune(gwn_model_s* m) {
     // 2D leaves have no separate factor (0 = beta); 3D leaves: per-level factors
     const double leafb[] = {0.0, 2.0, 2.5, 3.0, 4.0, 5.0};
     double best_cost = 1e300, best_b = 0, best_bl = 0;
+    std::vector<std::tuple<double, double, double>> ok_cands;  // (counted flops, beta, beta_leaf)
     double fb_err = 1e300, fb_b = 0, fb_bl = 0;  // fallback: smallest error seen
     const double tol = 0.5 * m->opts.tolerance;
     for (double b : betas) {
@@ -798,6 +812,7 @@ static gwn_status autotune(gwn_model_s* m) {
                              H.n_leaves, b, blv, e, cost / nv);
             if (e <= tol) {
                 any_ok = true;
+                ok_cands.push_back({cost, b, blv});
                 if (cost < best_cost) {
                     best_cost = cost;
                     best_b = b;
@@ -807,10 +822,10 @@ static gwn_status autotune(gwn_model_s* m) {
         }
         if (any_ok && best_b > 0 && b > 2.0 * best_b) break;  // larger beta only costs more
     }
-    cudaFree(dp);
     cudaFree(ref);
     cudaFree(w);
     cudaFree(err);
+    cudaFree(dp);
     if (s != GWN_OK) return s;
     if (best_b == 0) {  // nothing met the tolerance: the most accurate candidate tried
         best_b = fb_b > 0 ? fb_b : 8.0;
@@ -818,6 +833,83 @@ static gwn_status autotune(gwn_model_s* m) {
     }
     m->opts.beta = best_b;
     m->opts.beta_leaf = d == 3 ? best_bl : 0.0;
+    // Counted flops do not weigh the kernels alike (the traversal's far tests and
+    // Taylor terms issue about twice the instructions per counted flop of the
+    // node-table leaves), so among the accurate candidates the cheapest four by
+    // count are timed on a uniform sample of the model's box, and the fastest
+    // is kept; then the binning resolution is timed the same way.
+    if (ok_cands.size() > 1 || d == 3) {
+        std::sort(ok_cands.begin(), ok_cands.end());
+        if (ok_cands.size() > 4) ok_cands.resize(4);
+        const int nt = 1 << 16;
+        std::vector<float> tp((size_t)nt * d);
+        for (int i = 0; i < nt; ++i)
+            for (int k = 0; k < d; ++k) tp[(size_t)i * d + k] = (float)(H.lo[k] + rnd() * (H.hi[k] - H.lo[k]));
+        float* dt = nullptr;
+        double* wt = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool ok = cudaMalloc(&dt, tp.size() * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&wt, (size_t)nt * sizeof(double)) == cudaSuccess &&
+                  cudaMemcpy(dt, tp.data(), tp.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+                  ensure_workspace(m, nt, 0) == GWN_OK;
+        // best of two timed runs after one untimed run (microseconds)
+        auto timed = [&](double b, double bl) -> double {
+            gwn_query_opts q3;
+            gwn_default_query_opts(&q3);
+            q3.beta = b;
+            q3.beta_leaf = bl;
+            float best = 1e30f;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                ok = cudaEventRecord(e0, 0) == cudaSuccess &&
+                     gwn_enqueue_device(m, dt, GWN_F32, nt, wt, nullptr, nullptr, q3, 0, m->ws) == GWN_OK &&
+                     cudaEventRecord(e1, 0) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+                float ms = 0;
+                if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, ms);
+            }
+            return 1e3 * best;
+        };
+        double best_t = 1e300;
+        if (ok_cands.size() > 1) {
+            for (const auto& c : ok_cands) {
+                const double tus = timed(std::get<1>(c), std::get<2>(c));
+                if (std::getenv("GWN_AUTOTUNE_VERBOSE"))
+                    std::fprintf(stderr, "[gwn autotune] beta=%.1f beta_leaf=%.1f: %.1f us for %d points\n",
+                                 std::get<1>(c), std::get<2>(c), tus, nt);
+                if (ok && tus < best_t) {
+                    best_t = tus;
+                    m->opts.beta = std::get<1>(c);
+                    m->opts.beta_leaf = d == 3 ? std::get<2>(c) : 0.0;
+                }
+            }
+        }
+        if (d == 3 && ok) {
+            const double bl = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
+            int best_bits = m->bin_bits3;
+            double bt = 1e300;
+            for (int bits = 4; bits <= 6; ++bits) {
+                m->bin_bits3 = bits;
+                const double tus = timed(m->opts.beta, bl);
+                if (ok && tus < bt) {
+                    bt = tus;
+                    best_bits = bits;
+                }
+            }
+            m->bin_bits3 = best_bits;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(dt);
+        cudaFree(wt);
+        if (!ok) return fail(GWN_ERR_CUDA, "autotune timing failed");
+    }
+    // the tuning workspace is not the model's: the first query sizes its own
+    if (m->ws_mem) {
+        cudaFree(m->ws_mem);
+        m->ws_mem = nullptr;
+        m->ws_n = 0;
+        m->ws_bytes = 0;
+    }
     return GWN_OK;
 }
 
@@ -1114,6 +1206,8 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
     }
     s->beta_leaf = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
     s->device = m->device;
+    s->bin_bits = m->dim == 3 ? m->bin_bits3 : kBinBits2;
+    s->stack_depth = m->stack_depth;
     return GWN_OK;
 }
 
@@ -1152,7 +1246,7 @@ gwn_status gwn_model_tree(gwn_model m, int32_t* child, double* x0, double* r, do
 
 namespace {
 constexpr char kModelMagic[8] = {'G', 'W', 'N', 'M', 'O', 'D', 'E', 'L'};
-constexpr uint32_t kModelVersion = 3;
+constexpr uint32_t kModelVersion = 4;
 
 template <typename V>
 bool write_vec(FILE* f, const std::vector<V>& v) {
@@ -1240,7 +1334,7 @@ gwn_status gwn_model_save(gwn_model m, const char* path) {
     if (!f) return fail(GWN_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
     const int32_t hdr[4] = {(int32_t)kModelVersion, m->dim, m->leaf_far, (int32_t)sizeof(gwn_build_opts)};
     const HostModel& H = m->host;
-    const int32_t hm[3] = {H.dim, H.n_leaves, H.max_depth};
+    const int32_t hm[4] = {H.dim, H.n_leaves, H.max_depth, m->bin_bits3};
     bool ok = std::fwrite(kModelMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               std::fwrite(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
               std::fwrite(&m->opts, sizeof(gwn_build_opts), 1, f) == 1 && std::fwrite(hm, sizeof(hm), 1, f) == 1 &&
@@ -1261,7 +1355,7 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         return fail(GWN_ERR_OOM, "host allocation failed");
     }
     char magic[8] = {};
-    int32_t hdr[4] = {}, hm[3] = {};
+    int32_t hdr[4] = {}, hm[4] = {};
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kModelMagic, 8) == 0 &&
               std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == (int32_t)kModelVersion &&
               (hdr[1] == 2 || hdr[1] == 3) && hdr[3] == (int32_t)sizeof(gwn_build_opts) &&
@@ -1288,8 +1382,10 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         H.dim = hm[0];
         H.n_leaves = hm[1];
         H.max_depth = hm[2];
+        m->bin_bits3 = hm[3];
+        ok = hm[3] >= 4 && hm[3] <= 6;
         // consistency of the arrays the kernels index
-        ok = host_model_consistent(H, m->dim);
+        ok = ok && host_model_consistent(H, m->dim);
     }
     if (!ok || check_opts(m->opts) != GWN_OK) {
         delete m;

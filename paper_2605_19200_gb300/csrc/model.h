@@ -18,6 +18,11 @@ struct gwn_model_s {
     int device = 0;
     int64_t n_primitives = 0;
     gwn_build_opts opts{};
+    // launch parameters of the 3D query, set by the autotuner: Morton-cell bits
+    // per axis of the spatial binning (4..6) and warp-stack entries of the
+    // packet traversal (64, 96 or 128, from the tree depth)
+    int bin_bits3 = 5;
+    int stack_depth = 96;
     double build_ms = 0;
     gwn::HostModel host;       // host copy (inspection)
     gwn::DevTree tree{};

@@ -32,7 +32,8 @@
 namespace gwn {
 
 constexpr int kBinBits2 = 9;   // 512 x 512 cells in 2D
-constexpr int kBinBits3 = 5;   // 32^3 cells in 3D
+constexpr int kBinBits3 = 5;   // 32^3 cells in 3D (default; the autotuner picks 4, 5 or 6 per model)
+constexpr int kMaxBinCells = 1 << 18;  // 2^(2 x 9) = 2^(3 x 6)
 constexpr uint32_t kPairOverflow = 0x100u;  // internal status bit: the point's pairs did not fit
 
 
@@ -70,12 +71,11 @@ __device__ __forceinline__ void load_point_f(const void* pts, int dtype, int dim
 }
 
 template <int DIM>
-__global__ void k_bin(const void* pts, int dtype, int n, float3 lo, float3 inv, int* key, int* hist) {
+__global__ void k_bin(const void* pts, int dtype, int n, float3 lo, float3 inv, int bits, int* key, int* hist) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float q[3] = {0, 0, 0};
     load_point_f(pts, dtype, DIM, i, q);
-    const int bits = DIM == 2 ? kBinBits2 : kBinBits3;
     const float cells = (float)(1 << bits);
     float l[3] = {lo.x, lo.y, lo.z}, s[3] = {inv.x, inv.y, inv.z};
     uint32_t c[3];
@@ -162,12 +162,15 @@ __device__ __forceinline__ void flush_warp_pairs(const int2* buf, const unsigned
 // part with an empty mask).
 // n_dev != nullptr: the point list `perm` holds *n_dev entries (a later round
 // over the points whose pairs overflowed; their indices go to `olist_out`)
-constexpr int kPacketStack = 96;  // entries per warp
+// STACK: entries of the warp stack (pending second children along the packet's
+// path), chosen per model from its tree depth (64, 96 or 128)
+constexpr int kPacketStack = 96;  // entries per warp of the 2D traversal
 
+template <int STACK>
 __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int dtype, int n, const int* perm,
                                                float beta2, float beta2l, Workspace ws, unsigned long long* work,
                                                const int* n_dev, int* olist_out) {
-    __shared__ int2 sstk[4][kPacketStack];
+    __shared__ int2 sstk[4][STACK];
     __shared__ int2 sbuf[4][kPairBuf];
     __shared__ unsigned char sown[4][kPairBuf];
     const unsigned full = 0xffffffffu;
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
             const unsigned near = __ballot_sync(full, mine && !far);
             if (near) {
                 const int2 ch = GWN_LDG(t.child + node);
-                if (sp < kPacketStack) {
+                if (sp < STACK) {
                     if (lane == 0) stk[sp] = make_int2(ch.y, (int)near);
                     ++sp;
                 } else if ((near >> lane) & 1u) {

@@ -391,7 +391,7 @@ def main():
         f"{[(round(m.info()['beta'], 1), round(m.info()['beta_leaf'], 1)) for m in models]}")
     total_q = sum(p.shape[0] for p in points)
     tuned = [(round(m.info()["beta"], 2), round(m.info()["beta_leaf"], 2)) for m in models]
-    knobs = [(m.info()["bin_bits"], m.info()["stack_depth"]) for m in models]
+    knobs = [(m.info()["bin_points_per_cell"], m.info()["stack_depth"]) for m in models]
     n_leaves = sum(m.info()["n_leaves"] for m in models)
     n_patches = sum(len(p) for p, _ in workload)
     stream = torch.cuda.current_stream(dev)
@@ -606,7 +606,7 @@ def main():
         "config": {"workload": WORKLOAD_NAME,
                    "models": len(models), "patches": n_patches, "leaves": n_leaves, "queries_per_step": total_q,
                    "beta": "autotuned" if args.beta == 0 else args.beta, "beta_per_model": tuned,
-                   "bin_bits_stack_depth_per_model": knobs,
+                   "bin_points_per_cell_stack_depth_per_model": knobs,
                    "tolerance": 1e-4, "order": 2, "precision": "fp32 bulk + fp64 repair",
                    "l2": f"inputs larger than L2 ({total_q * 12 / 1e6:.0f} MB of points per step)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1),

@@ -104,8 +104,8 @@ typedef struct {
     double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2, or 0 = autotune:
                              among the (beta, beta_leaf) pairs whose FP32 error on validation points
                              (FP64 direct sum on the device) stays below tolerance / 2, the fastest on
-                             a timed uniform sample, then the binning resolution by measured time
-                             (default 2) */
+                             a timed uniform sample, then the binning's points per cell by measured
+                             time (default 2) */
     double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves;
                              < 0 = automatic: direct sum up to 512 leaves, else 3 x beta (default -1) */
     double repair_band;   /* re-evaluate in FP64 when |w - round(w) +- 1/2| < band (default 1e-3) */
@@ -123,6 +123,11 @@ typedef struct {
                               beyond beta * s * r with s = clamp((a / median a)^(1 / (order + d)), 1, 4),
                               since its order-p remainder grows like a * beta^-(p + d); dense clusters are
                               opened earlier, the others keep beta.  0 = off (default 0) */
+    int32_t device_build;  /* 3D: the per-leaf stage of the build -- leaf moments (Section 3.1) and the
+                              packing of the leaves' boundary curves for the near field -- on the model's
+                              GPU, one thread per leaf or curve (1), or on the host threads (0); both give
+                              the same model bit for bit.  -1 = on the GPU unless the build is host-only
+                              (default -1) */
 } gwn_build_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -212,8 +217,10 @@ typedef struct {
     double lo[3], hi[3];    /* box of all control points */
     double beta_leaf;       /* far-test factor of the leaves (3D; equals beta unless set or tuned) */
     int32_t device;         /* CUDA ordinal holding the model, or GWN_DEVICE_HOST_ONLY */
-    int32_t bin_bits;       /* Morton-cell bits per axis of the query's spatial binning (3D: picked by
-                               the autotuner from 4..6 by measured time; 2D: 9) */
+    int32_t bin_points_per_cell; /* 3D: points per Morton cell the query's spatial binning aims at (a chunk
+                               of n points is binned with round(log2(n / this) / 3) bits per axis, 3..6);
+                               picked by the autotuner from 4, 16, 64 by measured time (default 16).
+                               2D: 0 (9 bits per axis) */
     int32_t stack_depth;    /* warp-stack entries of the packet traversal (from the tree depth) */
 } gwn_model_stats;
 

@@ -50,7 +50,7 @@ class gwn_build_opts(ctypes.Structure):
                 ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double), ("repair_band", ctypes.c_double),
                 ("quad_nodes", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("n_threads", ctypes.c_int32), ("leaf_far", ctypes.c_int32), ("beta_leaf", ctypes.c_double),
-                ("adaptive_beta", ctypes.c_int32)]
+                ("adaptive_beta", ctypes.c_int32), ("device_build", ctypes.c_int32)]
 
 
 class gwn_query_opts(ctypes.Structure):
@@ -65,7 +65,7 @@ class gwn_model_stats(ctypes.Structure):
                 ("build_ms", ctypes.c_double), ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double),
                 ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double), ("device", ctypes.c_int32),
-                ("bin_bits", ctypes.c_int32), ("stack_depth", ctypes.c_int32)]
+                ("bin_points_per_cell", ctypes.c_int32), ("stack_depth", ctypes.c_int32)]
 
 
 class gwn_serve_opts(ctypes.Structure):

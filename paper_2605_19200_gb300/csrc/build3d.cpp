@@ -31,6 +31,8 @@
 #include <thread>
 
 #include "build.h"
+#include "build_device.h"
+#include "curves3d.h"
 
 namespace gwn {
 
@@ -39,54 +41,8 @@ namespace {
 constexpr double kMaxConeDeg = 55.0;
 constexpr int kMaxSplitDepth = 14;
 
-struct BinomTable {
-    double T[40][40];
-    BinomTable() {
-        for (int a = 0; a < 40; ++a) {
-            for (int b = 0; b < 40; ++b) T[a][b] = 0.0;
-            T[a][0] = T[a][a] = 1.0;
-            for (int b = 1; b < a; ++b) T[a][b] = T[a - 1][b - 1] + T[a - 1][b];
-        }
-    }
-};
-
-double binom(int n, int k) {
-    static const BinomTable table;  // thread-safe one-time initialisation
-    return table.T[n][k];
-}
-
-// product of Bernstein polynomials a (degree m) and b (degree n)
-void bmul(const double* a, int m, const double* b, int n, double* c) {
-    for (int k = 0; k <= m + n; ++k) c[k] = 0;
-    for (int i = 0; i <= m; ++i)
-        for (int j = 0; j <= n; ++j) c[i + j] += binom(m, i) * binom(n, j) / binom(m + n, i + j) * a[i] * b[j];
-}
-
 // ---------------------------------------------------------------- 2D pieces
 
-struct TP {  // rational Bezier piece in (u, v), homogeneous (w u, w v, w)
-    int deg;
-    double h[4][3];
-};
-
-void tp_eval(const TP& p, double t, double* x, double* dx) {
-    double T[4][3];
-    std::memcpy(T, p.h, sizeof(T));
-    int n = p.deg;
-    double D[3] = {0, 0, 0};
-    for (int r = 1; r <= n; ++r) {
-        if (r == n && dx)
-            for (int k = 0; k < 3; ++k) D[k] = n * (T[1][k] - T[0][k]);
-        for (int i = 0; i <= n - r; ++i)
-            for (int k = 0; k < 3; ++k) T[i][k] = (1 - t) * T[i][k] + t * T[i + 1][k];
-    }
-    x[0] = T[0][0] / T[0][2];
-    x[1] = T[0][1] / T[0][2];
-    if (dx) {
-        dx[0] = (D[0] - x[0] * D[2]) / T[0][2];
-        dx[1] = (D[1] - x[1] * D[2]) / T[0][2];
-    }
-}
 
 void tp_split(const TP& p, double t, TP* L, TP* R) {
     double T[4][3];
@@ -114,25 +70,6 @@ TP tp_line(double u0, double v0, double u1, double v1) {
     p.h[0][0] = u0; p.h[0][1] = v0; p.h[0][2] = 1;
     p.h[1][0] = u1; p.h[1][1] = v1; p.h[1][2] = 1;
     return p;
-}
-
-TP tp_elevate3(const TP& p) {
-    TP q = p;
-    while (q.deg < 3) {
-        TP r;
-        int n = q.deg;
-        r.deg = n + 1;
-        for (int k = 0; k < 3; ++k) {
-            r.h[0][k] = q.h[0][k];
-            r.h[n + 1][k] = q.h[n][k];
-        }
-        for (int i = 1; i <= n; ++i) {
-            double a = (double)i / (n + 1);
-            for (int k = 0; k < 3; ++k) r.h[i][k] = a * q.h[i - 1][k] + (1 - a) * q.h[i][k];
-        }
-        q = r;
-    }
-    return q;
 }
 
 // roots in [0, 1] of sum B_i(t) cf_i, isolated by halving: no sign change in
@@ -224,36 +161,6 @@ int winding(const std::vector<TP>& pcs, const double* x) {
 }
 
 // ---------------------------------------------------------------- bicubic nets
-
-struct Net {
-    double h[4][4][4];  // [i_u][i_v] homogeneous (w x, w y, w z, w)
-};
-
-void net_eval(const Net& N, double u, double v, double* S, double* Su, double* Sv) {
-    double Bu[4], Bv[4], dBu[4], dBv[4];
-    auto bern = [](double t, double* B, double* dB) {
-        double s = 1 - t;
-        B[0] = s * s * s; B[1] = 3 * t * s * s; B[2] = 3 * t * t * s; B[3] = t * t * t;
-        dB[0] = -3 * s * s; dB[1] = 3 * s * s - 6 * t * s; dB[2] = 6 * t * s - 3 * t * t; dB[3] = 3 * t * t;
-    };
-    bern(u, Bu, dBu);
-    bern(v, Bv, dBv);
-    double H[4] = {0, 0, 0, 0}, Hu[4] = {0, 0, 0, 0}, Hv[4] = {0, 0, 0, 0};
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j)
-            for (int k = 0; k < 4; ++k) {
-                double h = N.h[i][j][k];
-                H[k] += Bu[i] * Bv[j] * h;
-                Hu[k] += dBu[i] * Bv[j] * h;
-                Hv[k] += Bu[i] * dBv[j] * h;
-            }
-    for (int k = 0; k < 3; ++k) S[k] = H[k] / H[3];
-    if (Su)
-        for (int k = 0; k < 3; ++k) {
-            Su[k] = (Hu[k] - S[k] * Hu[3]) / H[3];
-            Sv[k] = (Hv[k] - S[k] * Hv[3]) / H[3];
-        }
-}
 
 // restrict a bicubic net to [u0,u1] x [v0,v1] of its own [0,1]^2 domain
 Net net_sub(const Net& N, double u0, double u1, double v0, double v1) {
@@ -439,41 +346,10 @@ bool cone_ok(const Net& N, double* nrm) {
     return ok;
 }
 
-// moments by Green's theorem on the leaf's local boundary
+// moments by Green's theorem on the leaf's local boundary (leaf_moments_core)
 void leaf_moments(Leaf& L, const double* xref, const std::vector<double>& gx, const std::vector<double>& gw) {
-    std::fill(L.mom, L.mom + 39, 0.0);
-    L.area = 0;
-    L.ax[0] = L.ax[1] = L.ax[2] = 0;
-    const int n = (int)gx.size();
-    for (size_t pi = 0; pi < L.bnd.size(); ++pi) {
-        const TP& P = L.bnd[pi];
-        const double m = L.mult[pi];
-        for (int a = 0; a < n; ++a) {
-            double uv[2], duv[2];
-            tp_eval(P, gx[a], uv, duv);
-            double wo = m * gw[a] * duv[1];
-            if (wo == 0.0) continue;
-            for (int b = 0; b < n; ++b) {
-                double s = uv[0] * gx[b];
-                double wt = wo * uv[0] * gw[b];
-                double S[3], Su[3], Sv[3];
-                net_eval(L.net, s, uv[1], S, Su, Sv);
-                double N[3] = {Su[1] * Sv[2] - Su[2] * Sv[1], Su[2] * Sv[0] - Su[0] * Sv[2], Su[0] * Sv[1] - Su[1] * Sv[0]};
-                double nl = std::sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-                double x[3] = {S[0] - xref[0], S[1] - xref[1], S[2] - xref[2]};
-                for (int k = 0; k < 3; ++k) L.mom[k] += wt * N[k];
-                for (int i = 0; i < 3; ++i)
-                    for (int k = 0; k < 3; ++k) L.mom[3 + i * 3 + k] += wt * x[i] * N[k];
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j) {
-                        double xx = wt * x[i] * x[j];
-                        for (int k = 0; k < 3; ++k) L.mom[12 + (i * 3 + j) * 3 + k] += xx * N[k];
-                    }
-                L.area += wt * nl;
-                for (int k = 0; k < 3; ++k) L.ax[k] += wt * nl * S[k];
-            }
-        }
-    }
+    leaf_moments_core(L.net, L.bnd.data(), L.mult.data(), (int)L.bnd.size(), xref, gx.data(), gw.data(), (int)gx.size(),
+                      L.mom, &L.area, L.ax);
 }
 
 void gauss_legendre01(int n, std::vector<double>* x, std::vector<double>* w) {
@@ -498,161 +374,10 @@ void gauss_legendre01(int n, std::vector<double>* x, std::vector<double>* w) {
     }
 }
 
-// homogeneous point and derivative of a degree-D Bezier curve (D + 1 points of
-// 4 doubles in X) at t, by de Casteljau: the two points of the last-but-one
-// level give the derivative D (b1 - b0) and the point (1 - t) b0 + t b1
-void bez4_eval(const std::vector<double>& X, int D, double t, double P[4], double dP[4]) {
-    double b[kMaxC3Deg + 1][4];
-    for (int i = 0; i <= D; ++i)
-        for (int c = 0; c < 4; ++c) b[i][c] = X[(size_t)i * 4 + c];
-    for (int r = 1; r < D; ++r)
-        for (int i = 0; i <= D - r; ++i)
-            for (int c = 0; c < 4; ++c) b[i][c] = (1 - t) * b[i][c] + t * b[i + 1][c];
-    for (int c = 0; c < 4; ++c) {
-        dP[c] = D * (b[1][c] - b[0][c]);
-        P[c] = (1 - t) * b[0][c] + t * b[1][c];
-    }
-}
-
-// Panel level from which the 4-point Gauss-Legendre rule of the FP32 line
-// integral resolves the curve's own rational parametrisation.  The integrand
-// carries the tangent x'(t) = (X' W - X W') / W^2, whose poles (the complex
-// zeros of the weight W(t)) bound the rule's convergence: its error on a panel
-// falls like rho^-8, rho the Bernstein-ellipse parameter of the nearest pole.
-// On every panel of the returned level the rule must integrate x' itself --
-// whose exact integral is the chord x(b) - x(a) -- to 1e-6 of the panel's arc
-// length.  A quarter circle (weights 1, 1/sqrt 2, 1) composed with a bicubic
-// net has its poles at t = 1/2 +- 1.21 i: rho ~ 5 on [0, 1], ~ 10 on its halves.
-int curve_min_level(const std::vector<double>& X, int D, const std::vector<double>& x4, const std::vector<double>& w4) {
-    auto point = [&](double t, double x[3], double dx[3]) {
-        double P[4], dP[4];
-        bez4_eval(X, D, t, P, dP);
-        for (int c = 0; c < 3; ++c) {
-            x[c] = P[c] / P[3];
-            dx[c] = (dP[c] - x[c] * dP[3]) / P[3];
-        }
-    };
-    for (int L = 0; L < kMaxMinLevel; ++L) {
-        const int np = 1 << L;
-        const double h = 1.0 / np;
-        bool ok = true;
-        for (int p = 0; p < np && ok; ++p) {
-            double a[3], b[3], d[3], I[3] = {0, 0, 0}, arc = 0;
-            point(h * p, a, d);
-            point(h * (p + 1), b, d);
-            for (size_t k = 0; k < x4.size(); ++k) {
-                double x[3];
-                point(h * (p + x4[k]), x, d);
-                for (int c = 0; c < 3; ++c) I[c] += h * w4[k] * d[c];
-                arc += h * w4[k] * std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            }
-            const double e = std::sqrt((I[0] - (b[0] - a[0])) * (I[0] - (b[0] - a[0])) +
-                                       (I[1] - (b[1] - a[1])) * (I[1] - (b[1] - a[1])) +
-                                       (I[2] - (b[2] - a[2])) * (I[2] - (b[2] - a[2])));
-            ok = e <= 1e-6 * arc;
-        }
-        if (ok) return L;
-    }
-    return kMaxMinLevel;
-}
-
-// the node table of one boundary curve (Curve3Info / kC3NodeVec in
-// gwn_internal.h): positions relative to the leaf centre and derivatives at
-// the 4 Gauss-Legendre nodes of the level-0 panel and of the two level-1
-// panels, and each panel's length estimate (chords between the nodes x the
-// FP32 rule's span factor 1.17, as the kernels compute it)
-void node_table(const std::vector<double>& X, int D, const float cen[3], float mult, const std::vector<double>& x4,
-                float4 out[kC3NodeVec]) {
-    const double a0[3] = {0.0, 0.0, 0.5}, hh[3] = {1.0, 0.5, 0.5};
-    float len[3];
-    for (int p = 0; p < 3; ++p) {
-        float f[24];
-        double prev[3] = {0, 0, 0}, L = 0;
-        for (int k = 0; k < 4; ++k) {
-            double P[4], dP[4];
-            bez4_eval(X, D, a0[p] + hh[p] * x4[k], P, dP);
-            double x[3];
-            for (int c = 0; c < 3; ++c) {
-                x[c] = P[c] / P[3];
-                f[6 * k + c] = (float)(x[c] - (double)cen[c]);
-                f[6 * k + 3 + c] = (float)((dP[c] - x[c] * dP[3]) / P[3]);
-            }
-            if (k > 0) L += std::sqrt((x[0] - prev[0]) * (x[0] - prev[0]) + (x[1] - prev[1]) * (x[1] - prev[1]) +
-                                      (x[2] - prev[2]) * (x[2] - prev[2]));
-            for (int c = 0; c < 3; ++c) prev[c] = x[c];
-        }
-        len[p] = (float)(1.17 * L);
-        for (int v = 0; v < 6; ++v) out[1 + 6 * p + v] = float4{f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]};
-    }
-    out[0] = float4{len[0], len[1], len[2], mult};
-}
-
-// the FP64 node table of one boundary curve (kC3Node64 in gwn_internal.h):
-// absolute positions and tangents at the 8 Gauss-Legendre nodes of the level-0
-// panel and of the two level-1 panels, and the panels' length estimates with
-// the 8-point rule's span factor 1.1 (as the FP64 kernels compute them)
-void node_table64(const std::vector<double>& X, int D, double mult, const std::vector<double>& x8, double* out) {
-    const double a0[3] = {0.0, 0.0, 0.5}, hh[3] = {1.0, 0.5, 0.5};
-    for (int p = 0; p < 3; ++p) {
-        double* nodes = out + 4 + 48 * p;
-        double prev[3] = {0, 0, 0}, L = 0;
-        for (int k = 0; k < 8; ++k) {
-            double P[4], dP[4];
-            bez4_eval(X, D, a0[p] + hh[p] * x8[k], P, dP);
-            for (int c = 0; c < 3; ++c) {
-                const double x = P[c] / P[3];
-                nodes[6 * k + c] = x;
-                nodes[6 * k + 3 + c] = (dP[c] - x * dP[3]) / P[3];
-            }
-            const double* x = nodes + 6 * k;
-            if (k > 0) L += std::sqrt((x[0] - prev[0]) * (x[0] - prev[0]) + (x[1] - prev[1]) * (x[1] - prev[1]) +
-                                      (x[2] - prev[2]) * (x[2] - prev[2]));
-            for (int c = 0; c < 3; ++c) prev[c] = x[c];
-        }
-        out[p] = 1.1 * L;
-    }
-    out[3] = mult;
-}
-
-// compose a local (u, v) piece with the bicubic net: 4D rational Bezier of degree 6 deg
-void compose(const TP& p, const Net& N, std::vector<double>* X) {
-    int d = p.deg;
-    double U[4], V[4], W[4], WU[4], WV[4];
-    for (int i = 0; i <= d; ++i) {
-        U[i] = p.h[i][0];
-        V[i] = p.h[i][1];
-        W[i] = p.h[i][2];
-        WU[i] = W[i] - U[i];
-        WV[i] = W[i] - V[i];
-    }
-    // Upow[i] = U^i (W - U)^(3 - i), degree 3 d
-    double Up[4][13], Vp[4][13], tmp[13], tmp2[13];
-    for (int i = 0; i < 4; ++i) {
-        double cur[13] = {1.0};
-        int deg = 0;
-        for (int k = 0; k < i; ++k) { bmul(cur, deg, U, d, tmp); deg += d; std::memcpy(cur, tmp, sizeof(double) * (deg + 1)); }
-        for (int k = i; k < 3; ++k) { bmul(cur, deg, WU, d, tmp); deg += d; std::memcpy(cur, tmp, sizeof(double) * (deg + 1)); }
-        std::memcpy(Up[i], cur, sizeof(double) * (deg + 1));
-        double cv[13] = {1.0};
-        deg = 0;
-        for (int k = 0; k < i; ++k) { bmul(cv, deg, V, d, tmp2); deg += d; std::memcpy(cv, tmp2, sizeof(double) * (deg + 1)); }
-        for (int k = i; k < 3; ++k) { bmul(cv, deg, WV, d, tmp2); deg += d; std::memcpy(cv, tmp2, sizeof(double) * (deg + 1)); }
-        std::memcpy(Vp[i], cv, sizeof(double) * (deg + 1));
-    }
-    const int D = 6 * d;
-    X->assign((size_t)(D + 1) * 4, 0.0);
-    double prod[19];
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) {
-            bmul(Up[i], 3 * d, Vp[j], 3 * d, prod);
-            double c = binom(3, i) * binom(3, j);
-            for (int t = 0; t <= D; ++t)
-                for (int k = 0; k < 4; ++k) (*X)[t * 4 + k] += c * prod[t] * N.h[i][j][k];
-        }
-}
-
+// leaves of one patch; with `moments` their moments too (else the device
+// stage computes them)
 void make_leaves(const PatchWork& P, const gwn_build_opts& o, double sdiag, const double* xref,
-                 const std::vector<double>& gx, const std::vector<double>& gw, std::vector<Leaf>* out) {
+                 const std::vector<double>& gx, const std::vector<double>& gw, bool moments, std::vector<Leaf>* out) {
     const double lim = o.max_aabb_frac > 0 ? o.max_aabb_frac * sdiag : 1e300;
     struct Item {
         Rect R;        // global
@@ -710,7 +435,7 @@ void make_leaves(const PatchWork& P, const gwn_build_opts& o, double sdiag, cons
         std::memcpy(L.lo, lo, sizeof(lo));
         std::memcpy(L.hi, hi, sizeof(hi));
         std::memcpy(L.nrm, nrm, sizeof(nrm));
-        leaf_moments(L, xref, gx, gw);
+        if (moments) leaf_moments(L, xref, gx, gw);
         out->push_back(std::move(L));
     }
 }
@@ -749,69 +474,25 @@ struct LeafPack {
 
 void pack_leaf(const Leaf& L, const float cen[3], const std::vector<double>& g4x, const std::vector<double>& g4w,
                const std::vector<double>& g8x, LeafPack* P) {
-    std::vector<double> X;
-    for (size_t b = 0; b < L.bnd.size(); ++b) {
-        compose(L.bnd[b], L.net, &X);
-        int D = 6 * L.bnd[b].deg;
-        Curve3Info ci;
-        ci.ctrl_off = (int32_t)P->c3pts.size();
-        ci.deg = D;
-        ci.mult = (float)L.mult[b];
-        ci.min_level = curve_min_level(X, D, g4x, g4w);
-        P->c3.push_back(ci);
-        {
-            float4 tab[kC3NodeVec];
-            node_table(X, D, cen, ci.mult, g4x, tab);
-            P->c3n.insert(P->c3n.end(), tab, tab + kC3NodeVec);
-            double tab64[kC3Node64];
-            node_table64(X, D, (double)L.mult[b], g8x, tab64);
-            P->c3n64.insert(P->c3n64.end(), tab64, tab64 + kC3Node64);
-        }
-        // D + 1 points scaled by C(D, i), then D derivative points C(D-1, i) (c_{i+1} - c_i),
-        // then the same 2 D + 1 points of the reversed curve (evaluation for t > 1/2);
-        // float copies relative to the leaf centre, double copies absolute
-        std::vector<double> rel((size_t)(D + 1) * 4);
-        for (int t = 0; t <= D; ++t) {
-            const double* h = &X[(size_t)t * 4];
-            double r4[4] = {h[0] - cen[0] * h[3], h[1] - cen[1] * h[3], h[2] - cen[2] * h[3], h[3]};
-            for (int k = 0; k < 4; ++k) rel[(size_t)t * 4 + k] = r4[k];
-            double c = binom(D, t);
-            P->c3pts.push_back(float4{(float)(c * r4[0]), (float)(c * r4[1]), (float)(c * r4[2]), (float)(c * r4[3])});
-            for (int k = 0; k < 4; ++k) P->c3pts64.push_back(c * h[k]);
-        }
-        for (int t = 0; t < D; ++t) {
-            double c = binom(D - 1, t);
-            float f[4];
-            for (int k = 0; k < 4; ++k) {
-                f[k] = (float)(c * (rel[(size_t)(t + 1) * 4 + k] - rel[(size_t)t * 4 + k]));
-                P->c3pts64.push_back(c * (X[(size_t)(t + 1) * 4 + k] - X[(size_t)t * 4 + k]));
-            }
-            P->c3pts.push_back(float4{f[0], f[1], f[2], f[3]});
-        }
-        {
-            // reversed copy: R_i = P_{D-i}, RQ_i = Q_{D-1-i}
-            const size_t f0 = (size_t)ci.ctrl_off, d0 = (size_t)ci.ctrl_off * 4;
-            for (int t = 0; t <= D; ++t) {
-                P->c3pts.push_back(P->c3pts[f0 + (size_t)(D - t)]);
-                for (int k = 0; k < 4; ++k) P->c3pts64.push_back(P->c3pts64[d0 + (size_t)(D - t) * 4 + k]);
-            }
-            for (int t = 0; t < D; ++t) {
-                P->c3pts.push_back(P->c3pts[f0 + (size_t)(D + 1 + D - 1 - t)]);
-                for (int k = 0; k < 4; ++k)
-                    P->c3pts64.push_back(P->c3pts64[d0 + (size_t)(D + 1 + D - 1 - t) * 4 + k]);
-            }
-        }
-        TP e3 = tp_elevate3(L.bnd[b]);
-        float f[12];
-        for (int t = 0; t < 4; ++t)
-            for (int k = 0; k < 3; ++k) {
-                f[t * 3 + k] = (float)e3.h[t][k];
-                P->c2_64.push_back(e3.h[t][k]);
-            }
-        P->c2.push_back(float4{f[0], f[1], f[2], f[3]});
-        P->c2.push_back(float4{f[4], f[5], f[6], f[7]});
-        P->c2.push_back(float4{f[8], f[9], f[10], f[11]});
-        P->c2mult.push_back((float)L.mult[b]);
+    const size_t nb = L.bnd.size();
+    P->c3.resize(nb);
+    P->c3n.resize(nb * kC3NodeVec);
+    P->c3n64.resize(nb * kC3Node64);
+    P->c2.resize(nb * kC2Vec);
+    P->c2_64.resize(nb * 12);
+    P->c2mult.resize(nb);
+    size_t npts = 0;
+    for (size_t b = 0; b < nb; ++b) npts += 2 * (2 * 6 * (size_t)L.bnd[b].deg + 1);
+    P->c3pts.resize(npts);
+    P->c3pts64.resize(npts * 4);
+    size_t off = 0;
+    for (size_t b = 0; b < nb; ++b) {
+        Curve3Info& ci = P->c3[b];
+        ci.ctrl_off = (int32_t)off;
+        pack_curve(L.bnd[b], L.mult[b], L.net, cen, g4x.data(), g4w.data(), g8x.data(), &ci, &P->c3pts[off],
+                   &P->c3pts64[off * 4], &P->c3n[b * kC3NodeVec], &P->c3n64[b * kC3Node64], &P->c2[b * kC2Vec],
+                   &P->c2_64[b * 12], &P->c2mult[b]);
+        off += 2 * (2 * (size_t)ci.deg + 1);
     }
 }
 
@@ -936,6 +617,9 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
     for (int k = 0; k < 3; ++k) xref[k] = 0.5 * (slo[k] + shi[k]);
     std::vector<double> gx, gw;
     gauss_legendre01(o.quad_nodes, &gx, &gw);
+    // the per-leaf stage (moments, boundary curves) on the model's GPU, unless
+    // the build is host-only or asks for the host stage
+    const bool dev = o.device_build != 0 && o.device != GWN_DEVICE_HOST_ONLY;
 
     // leaves of every patch, in parallel over patches
     int nt = o.n_threads > 0 ? o.n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
@@ -943,7 +627,7 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
     std::vector<std::vector<Leaf>> per(n);
     std::atomic<size_t> next{0};
     auto worker = [&]() {
-        for (size_t i; (i = next.fetch_add(1)) < n;) make_leaves(work[i], o, sdiag, xref, gx, gw, &per[i]);
+        for (size_t i; (i = next.fetch_add(1)) < n;) make_leaves(work[i], o, sdiag, xref, gx, gw, !dev, &per[i]);
     };
     std::vector<std::thread> th;
     for (int t = 1; t < nt; ++t) th.emplace_back(worker);
@@ -958,6 +642,30 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
     }
 
     const int nl = (int)leaves.size();
+    if (dev) {
+        // leaf moments on the device, one thread per leaf
+        std::vector<Net> nets(nl);
+        std::vector<TP> pieces;
+        std::vector<double> mult, mom, area_ax;
+        std::vector<int> off(nl + 1, 0);
+        for (int i = 0; i < nl; ++i) {
+            nets[i] = leaves[i].net;
+            pieces.insert(pieces.end(), leaves[i].bnd.begin(), leaves[i].bnd.end());
+            mult.insert(mult.end(), leaves[i].mult.begin(), leaves[i].mult.end());
+            off[i + 1] = (int)pieces.size();
+        }
+        std::string e = device_leaf_moments(nets, pieces, mult, off, xref, gx, gw, &mom, &area_ax);
+        if (!e.empty()) {
+            *code = GWN_ERR_CUDA;
+            return e;
+        }
+        for (int i = 0; i < nl; ++i) {
+            Leaf& L = leaves[i];
+            std::memcpy(L.mom, &mom[(size_t)i * 39], sizeof(L.mom));
+            L.area = area_ax[(size_t)i * 4];
+            for (int k = 0; k < 3; ++k) L.ax[k] = area_ax[(size_t)i * 4 + 1 + k];
+        }
+    }
     LeafSet S;
     S.dim = 3;
     std::memcpy(S.xref, xref, sizeof(xref));
@@ -1023,13 +731,54 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
                 I.c3_cnt = (int32_t)L.bnd.size();
                 I.c2_cnt = (int32_t)L.bnd.size();
                 out->leaf3[i] = I;  // offsets follow when the pieces are concatenated
-                pack_leaf(L, cen, g4x, g4w, g8x, &packs[i]);
+                if (!dev) pack_leaf(L, cen, g4x, g4w, g8x, &packs[i]);
             }
         };
         std::vector<std::thread> pth;
         for (int t = 1; t < nt; ++t) pth.emplace_back(pack_worker);
         pack_worker();
         for (auto& t : pth) t.join();
+    }
+    if (dev) {
+        // the boundary curves on the device, one thread per curve, in BVH order
+        std::vector<Net> nets(nl);
+        std::vector<float> cen((size_t)nl * 3);
+        std::vector<TP> pieces;
+        std::vector<double> mult;
+        std::vector<int> cleaf;
+        std::vector<int32_t> coff;
+        size_t npts = 0;
+        for (int i = 0; i < nl; ++i) {
+            const Leaf& L = leaves[perm[i]];
+            Leaf3Info& I = out->leaf3[i];
+            nets[i] = L.net;
+            for (int k = 0; k < 3; ++k) cen[(size_t)i * 3 + k] = I.cen[k];
+            I.c3_off = (int32_t)pieces.size();
+            I.c2_off = I.c3_off;
+            for (size_t b = 0; b < L.bnd.size(); ++b) {
+                pieces.push_back(L.bnd[b]);
+                mult.push_back(L.mult[b]);
+                cleaf.push_back(i);
+                coff.push_back((int32_t)npts);
+                npts += 2 * (2 * 6 * (size_t)L.bnd[b].deg + 1);
+            }
+        }
+        const size_t nc = pieces.size();
+        out->c3.resize(nc);
+        out->c3pts.resize(npts);
+        out->c3pts64.resize(npts * 4);
+        out->c3n.resize(nc * kC3NodeVec);
+        out->c3n64.resize(nc * kC3Node64);
+        out->c2.resize(nc * kC2Vec);
+        out->c2_64.resize(nc * 12);
+        out->c2mult.resize(nc);
+        std::string e = device_pack_curves(nets, cen, pieces, mult, cleaf, coff, g4x, g4w, g8x, out);
+        if (!e.empty()) {
+            *code = GWN_ERR_CUDA;
+            return e;
+        }
+        *code = GWN_OK;
+        return "";
     }
     for (int i = 0; i < nl; ++i) {
         LeafPack& P = packs[i];

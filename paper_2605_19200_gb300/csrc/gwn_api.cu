@@ -227,6 +227,7 @@ gwn_status check_opts(const gwn_build_opts& o) {
     if (!(o.beta_leaf == 0.0 || o.beta_leaf >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_leaf must be 0 or >= 2");
     if (o.order < 0 || o.order > 2) return fail(GWN_ERR_INVALID_ARG, "order must be 0, 1 or 2");
     if (o.adaptive_beta != 0 && o.adaptive_beta != 1) return fail(GWN_ERR_INVALID_ARG, "adaptive_beta must be 0 or 1");
+    if (o.device_build < -1 || o.device_build > 1) return fail(GWN_ERR_INVALID_ARG, "device_build must be -1, 0 or 1");
     if (!(o.beta_repair <= 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be <= 0 or >= 2");
     if (!(o.repair_band >= 0.0 && o.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
     if (o.quad_nodes < 1 || o.quad_nodes > 32) return fail(GWN_ERR_INVALID_ARG, "quad_nodes must be 1..32");
@@ -446,6 +447,14 @@ gwn_status ensure_workspace(gwn_model_s* m, size_t n, size_t stage_bytes) {
 
 }  // namespace
 
+// Morton-cell bits per axis of the 3D binning of a chunk of n points: about
+// ppc points per cell, 3..6 bits
+static int bin_bits3(size_t n, int ppc) {
+    const double cells = std::max(1.0, (double)n / std::max(1, ppc));
+    const int b = (int)std::lround(std::log2(cells) / 3.0);
+    return std::min(6, std::max(3, b));
+}
+
 // the kernels' parameters of one query
 static QueryParams query_params(const gwn_model_s* m, const gwn_query_opts& qo, const Workspace& ws) {
     QueryParams p;
@@ -550,7 +559,7 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         // 1. spatial binning of the points (counting sort by Morton cell)
         const int* perm = nullptr;
         if (n >= 2048) {
-            const int bits = m->dim == 2 ? kBinBits2 : m->bin_bits3;
+            const int bits = m->dim == 2 ? kBinBits2 : bin_bits3(n, m->bin_ppc);
             const int cells = 1 << (m->dim * bits);
             float3 lo = make_float3((float)m->host.lo[0], (float)m->host.lo[1], (float)m->host.lo[2]);
             float ex[3];
@@ -688,6 +697,7 @@ void gwn_default_build_opts(gwn_build_opts* o) {
     o->leaf_far = -1;
     o->beta_leaf = 0.0;
     o->adaptive_beta = 0;
+    o->device_build = -1;
 }
 
 void gwn_default_query_opts(gwn_query_opts* q) {
@@ -837,7 +847,8 @@ static gwn_status autotune(gwn_model_s* m) {
     // Taylor terms issue about twice the instructions per counted flop of the
     // node-table leaves), so among the accurate candidates the cheapest four by
     // count are timed on a uniform sample of the model's box, and the fastest
-    // is kept; then the binning resolution is timed the same way.
+    // is kept; then the binning's target points per cell is timed the same way
+    // (the sample is binned at the resolution its size gives, as a query is).
     if (ok_cands.size() > 1 || d == 3) {
         std::sort(ok_cands.begin(), ok_cands.end());
         if (ok_cands.size() > 4) ok_cands.resize(4);
@@ -885,17 +896,17 @@ static gwn_status autotune(gwn_model_s* m) {
         }
         if (d == 3 && ok) {
             const double bl = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
-            int best_bits = m->bin_bits3;
+            int best_ppc = m->bin_ppc;
             double bt = 1e300;
-            for (int bits = 4; bits <= 6; ++bits) {
-                m->bin_bits3 = bits;
+            for (int ppc : {4, 16, 64}) {
+                m->bin_ppc = ppc;
                 const double tus = timed(m->opts.beta, bl);
                 if (ok && tus < bt) {
                     bt = tus;
-                    best_bits = bits;
+                    best_ppc = ppc;
                 }
             }
-            m->bin_bits3 = best_bits;
+            m->bin_ppc = best_ppc;
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -930,6 +941,8 @@ static gwn_status build_common(int dim, const void* prims, size_t n, const gwn_b
     m->n_primitives = (int64_t)n;
     gwn_status code = GWN_OK;
     std::string err;
+    // the device stage of the 3D build runs on the model's device
+    DeviceGuard dg(o.device == GWN_DEVICE_HOST_ONLY ? -1 : o.device);
     try {
         if (dim == 2) err = build_model_2d(reinterpret_cast<const gwn_curve2d*>(prims), n, o, &m->host, &code);
         else err = build_model_3d(reinterpret_cast<const gwn_patch3d*>(prims), n, o, &m->host, &code);
@@ -1206,7 +1219,7 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
     }
     s->beta_leaf = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
     s->device = m->device;
-    s->bin_bits = m->dim == 3 ? m->bin_bits3 : kBinBits2;
+    s->bin_points_per_cell = m->dim == 3 ? m->bin_ppc : 0;
     s->stack_depth = m->stack_depth;
     return GWN_OK;
 }
@@ -1334,7 +1347,7 @@ gwn_status gwn_model_save(gwn_model m, const char* path) {
     if (!f) return fail(GWN_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
     const int32_t hdr[4] = {(int32_t)kModelVersion, m->dim, m->leaf_far, (int32_t)sizeof(gwn_build_opts)};
     const HostModel& H = m->host;
-    const int32_t hm[4] = {H.dim, H.n_leaves, H.max_depth, m->bin_bits3};
+    const int32_t hm[4] = {H.dim, H.n_leaves, H.max_depth, m->bin_ppc};
     bool ok = std::fwrite(kModelMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               std::fwrite(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
               std::fwrite(&m->opts, sizeof(gwn_build_opts), 1, f) == 1 && std::fwrite(hm, sizeof(hm), 1, f) == 1 &&
@@ -1382,8 +1395,8 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         H.dim = hm[0];
         H.n_leaves = hm[1];
         H.max_depth = hm[2];
-        m->bin_bits3 = hm[3];
-        ok = hm[3] >= 4 && hm[3] <= 6;
+        m->bin_ppc = hm[3];
+        ok = hm[3] >= 1 && hm[3] <= 4096;
         // consistency of the arrays the kernels index
         ok = ok && host_model_consistent(H, m->dim);
     }

@@ -18,10 +18,12 @@ struct gwn_model_s {
     int device = 0;
     int64_t n_primitives = 0;
     gwn_build_opts opts{};
-    // launch parameters of the 3D query, set by the autotuner: Morton-cell bits
-    // per axis of the spatial binning (4..6) and warp-stack entries of the
-    // packet traversal (64, 96 or 128, from the tree depth)
-    int bin_bits3 = 5;
+    // launch parameters of the 3D query: the spatial binning aims at this many
+    // points per Morton cell (a chunk of n points gets 3 log2(n / ppc) / 3 bits,
+    // 3..6 per axis; picked by the autotuner from 4, 16, 64 by measured time),
+    // and the packet traversal's warp stack (64, 96 or 128 entries, from the
+    // tree depth)
+    int bin_ppc = 16;
     int stack_depth = 96;
     double build_ms = 0;
     gwn::HostModel host;       // host copy (inspection)

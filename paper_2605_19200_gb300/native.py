@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(HERE, "libgwn.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["gwn_api.cu", "gwn_serve.cu", "gwn_batch.cu"]
+CU_SOURCES = ["gwn_api.cu", "gwn_serve.cu", "gwn_batch.cu", "build_device.cu"]
+# the device stage of the build must round like the host stage: no fused multiply-adds
+CU_FLAGS = {"build_device.cu": ["-fmad=false"]}
 CPP_SOURCES = ["build.cpp", "build3d.cpp"]
 
 
@@ -53,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = []
     for s in cu:
         o = os.path.join(BUILD_DIR, s + ".o")
-        jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+        jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, *CU_FLAGS.get(s, []), "-Xcompiler", "-fPIC",
                      "-I", INCLUDE, "-c", os.path.join(CSRC, s), "-o", o])
     for s in cpp:
         o = os.path.join(BUILD_DIR, s + ".o")

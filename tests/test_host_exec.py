@@ -35,8 +35,9 @@ def hx():
         pytest.skip("nvcc not available")
     os.makedirs(OUT_DIR, exist_ok=True)
     csrc = os.path.join(ROOT, "paper_2605_19200_gb300", "csrc")
-    cmd = [nvcc, "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
-           "-I", csrc, SRC, os.path.join(csrc, "build.cpp"), os.path.join(csrc, "build3d.cpp"), "-o", LIB]
+    cmd = [nvcc, "-std=c++17", "-O2", "-fmad=false", "-gencode", "arch=compute_103a,code=sm_103a", "-Xcompiler",
+           "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", csrc, SRC, os.path.join(csrc, "build.cpp"),
+           os.path.join(csrc, "build3d.cpp"), os.path.join(csrc, "build_device.cu"), "-o", LIB]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     lib = ctypes.CDLL(LIB)
@@ -52,9 +53,15 @@ def hx():
     return lib
 
 
+def _hopts(**kw):
+    """Build options of a host-only build (the harness runs the host build stage)."""
+    kw.setdefault("device", -2)
+    return api.default_build_opts(**kw)
+
+
 def _run3(hx, patches, q, beta, beta_leaf, **kw):
     parr, keep = api.marshal_patches(patches)
-    o = api.default_build_opts(beta=beta, beta_leaf=beta_leaf, **kw)
+    o = _hopts(beta=beta, beta_leaf=beta_leaf, **kw)
     q = np.ascontiguousarray(q, dtype=np.float64)
     n = q.shape[0]
     d32, d64, b32 = np.zeros(n), np.zeros(n), np.zeros(n)
@@ -67,7 +74,7 @@ def _run3(hx, patches, q, beta, beta_leaf, **kw):
 
 def _run2(hx, curves, q, beta, work=None, **kw):
     arr, keep = api.marshal_curves(curves)
-    o = api.default_build_opts(beta=beta, **kw)
+    o = _hopts(beta=beta, **kw)
     q = np.ascontiguousarray(q, dtype=np.float64)
     n = q.shape[0]
     d32, d64, b32 = np.zeros(n), np.zeros(n), np.zeros(n)
@@ -341,7 +348,7 @@ def test_node_tables_match_the_full_evaluation(hx, shape):
     else:
         patches, q = configs.sphere_3d(n_queries=60)    # quarter circles: degree 12, minimum level 1
     parr, keep = api.marshal_patches(patches)
-    o = api.default_build_opts(beta=6.0, beta_leaf=4.0)
+    o = _hopts(beta=6.0, beta_leaf=4.0)
     qq = np.ascontiguousarray(q, dtype=np.float64)
     nmax = 4096
     size = qq.shape[0] * nmax
@@ -368,7 +375,7 @@ def test_fp64_node_tables_match_the_full_evaluation(hx, shape):
     else:
         patches, q = configs.sphere_3d(n_queries=60)
     parr, keep = api.marshal_patches(patches)
-    o = api.default_build_opts(beta=6.0, beta_leaf=4.0)
+    o = _hopts(beta=6.0, beta_leaf=4.0)
     qq = np.ascontiguousarray(q, dtype=np.float64)
     nmax = 4096
     fast, ex = np.zeros(qq.shape[0] * nmax), np.zeros(qq.shape[0] * nmax)

@@ -281,8 +281,10 @@ GWN_HD inline int curve_min_level(const double* X, int D, const double* x4, cons
 // positions relative to the leaf centre and tangents at the 4 Gauss-Legendre
 // nodes of the level-0 panel and of the two level-1 panels, and each panel's
 // length estimate (chords between the nodes x the FP32 rule's span factor 1.17,
-// as the kernels compute it)
-GWN_HD inline void node_table(const double* X, int D, const float cen[3], float mult, const double* x4,
+// as the kernels compute it).  A panel below the curve's minimum level gets an
+// infinite length, so the table itself tells the kernel to skip it (level 0)
+// or to leave the curve to the full evaluator (level 1).
+GWN_HD inline void node_table(const double* X, int D, const float cen[3], float mult, int min_level, const double* x4,
                               float4 out[kC3NodeVec]) {
     const double a0[3] = {0.0, 0.0, 0.5}, hh[3] = {1.0, 0.5, 0.5};
     float len[3];
@@ -308,9 +310,9 @@ GWN_HD inline void node_table(const double* X, int D, const float cen[3], float 
             out[1 + 6 * p + v].w = f[4 * v + 3];
         }
     }
-    out[0].x = len[0];
-    out[0].y = len[1];
-    out[0].z = len[2];
+    out[0].x = min_level >= 1 ? INFINITY : len[0];
+    out[0].y = min_level >= 2 ? INFINITY : len[1];
+    out[0].z = min_level >= 2 ? INFINITY : len[2];
     out[0].w = mult;
 }
 
@@ -389,7 +391,7 @@ GWN_HD inline void pack_curve(const TP& piece, double mult, const Net& net, cons
     ci->deg = D;
     ci->mult = (float)mult;
     ci->min_level = curve_min_level(X, D, x4, w4);
-    node_table(X, D, cen, ci->mult, x4, tab32);
+    node_table(X, D, cen, ci->mult, ci->min_level, x4, tab32);
     node_table64(X, D, mult, x8, tab64);
     curve_points(X, D, cen, pts32, pts64);
     TP e3 = tp_elevate3(piece);

@@ -35,6 +35,7 @@
 namespace gwn {
 
 constexpr int kLevel32 = 10;
+constexpr float kInfF = 3.0e38f;  // below it: a finite panel length in a node table
 constexpr int kLevel64 = 30;
 // panel length / distance-to-q bound of the 8-point rule: the quadrature error
 // of an analytic integrand decays like rho^-16 with rho the Bernstein-ellipse
@@ -608,11 +609,11 @@ GWN_HD inline bool leaf3_fast32(const DevTree& t, const Leaf3Info& I, const floa
     int nodes = 0;
     for (int c = 0; c < I.c3_cnt; ++c) {
         const float4* H = t.c3n + (size_t)(I.c3_off + c) * kC3NodeVec;
-        const float4 hd = GWN_LDG(H);  // len0, len1a, len1b, mult
-        const int ml = t.c3[I.c3_off + c].min_level;
-        if (ml > 1) return false;
-        float psum, dmin2;
-        if (ml == 0) {
+        // len0, len1a, len1b, mult; an infinite length marks a panel below the
+        // curve's minimum level (level 0: skipped; level 1: the full evaluator)
+        const float4 hd = GWN_LDG(H);
+        if (hd.x < kInfF) {
+            float psum, dmin2;
             fast_panel(H + 1, q, s, psum, dmin2);
             nodes += 4;
             if (hd.x * hd.x <= ratio2 * dmin2) {
@@ -624,7 +625,7 @@ GWN_HD inline bool leaf3_fast32(const DevTree& t, const Leaf3Info& I, const floa
         fast_panel(H + 7, q, s, pa, da);
         fast_panel(H + 13, q, s, pb, db);
         nodes += 8;
-        if (hd.y * hd.y > ratio2 * da || hd.z * hd.z > ratio2 * db) return false;
+        if (!(hd.y * hd.y <= ratio2 * da && hd.z * hd.z <= ratio2 * db)) return false;
         acc += hd.w * 0.5f * (pa + pb);
     }
     if (wl) wl->v[kWorkFastNodes] += (unsigned long long)nodes;  // kWorkLeaves counts the full evaluations

@@ -392,6 +392,7 @@ def main():
     total_q = sum(p.shape[0] for p in points)
     tuned = [(round(m.info()["beta"], 2), round(m.info()["beta_leaf"], 2)) for m in models]
     knobs = [(m.info()["bin_points_per_cell"], m.info()["stack_depth"]) for m in models]
+    repair_betas = [(round(m.info()["beta_repair"], 2), round(m.info()["beta_repair_leaf"], 2)) for m in models]
     n_leaves = sum(m.info()["n_leaves"] for m in models)
     n_patches = sum(len(p) for p, _ in workload)
     stream = torch.cuda.current_stream(dev)
@@ -594,10 +595,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_serve:
         serving = serving_leg(gwn, args.serve_seconds, log)
 
-    # kernels per chunk of up to 2^19 points: bin, scan, scatter; 3 rounds of traversal, pair key, scan,
-    # pair scatter, node-table pairs, full pairs (+ round switch x2); near band, overflow, finish, the
-    # chunk's own repair x3 (normally empty), counter accumulate; per query: repair x3 + its accumulate
-    launches_per_step = sum(30 * math.ceil(p.shape[0] / (1 << 19)) + 4 for p in points)
+    # kernels per chunk of up to 2^19 points: bin, scan, scatter; 3 rounds of traversal, pair histogram,
+    # scan, pair sort, node-table pairs, full pairs (+ round switch x2); near band, overflow, finish, the
+    # chunk's own repair x4 (normally empty), counter accumulate; per query: repair x4 + its accumulate
+    launches_per_step = sum(31 * math.ceil(p.shape[0] / (1 << 19)) + 5 for p in points)
     line = {
         "metric": "GWN queries/s (batched containment, 16 trimmed-NURBS models)",
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
@@ -607,6 +608,7 @@ def main():
                    "models": len(models), "patches": n_patches, "leaves": n_leaves, "queries_per_step": total_q,
                    "beta": "autotuned" if args.beta == 0 else args.beta, "beta_per_model": tuned,
                    "bin_points_per_cell_stack_depth_per_model": knobs,
+                   "repair_beta_per_model": repair_betas,
                    "tolerance": 1e-4, "order": 2, "precision": "fp32 bulk + fp64 repair",
                    "l2": f"inputs larger than L2 ({total_q * 12 / 1e6:.0f} MB of points per step)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1),

@@ -107,7 +107,10 @@ typedef struct {
                              a timed uniform sample, then the binning's points per cell by measured
                              time (default 2) */
     double beta_repair;   /* beta of the FP64 repair traversal; 0 = exact direct sum over all leaves;
-                             < 0 = automatic: direct sum up to 512 leaves, else 3 x beta (default -1) */
+                             < 0 = automatic: direct sum up to 512 leaves, else 3 x beta for nodes and
+                             3 x beta_leaf for leaves, factors the autotuner lowers (to 2 and 1.5 at
+                             least) while the repaired values of its validation points stay within
+                             1e-7 of the FP64 direct sum (default -1) */
     double repair_band;   /* re-evaluate in FP64 when |w - round(w) +- 1/2| < band (default 1e-3) */
     int32_t quad_nodes;   /* Gauss-Legendre nodes per rule for 3D moments (default 10) */
     int32_t precision;    /* GWN_PREC_* (default GWN_PREC_FP32_REPAIR) */
@@ -222,6 +225,7 @@ typedef struct {
                                picked by the autotuner from 4, 16, 64 by measured time (default 16).
                                2D: 0 (9 bits per axis) */
     int32_t stack_depth;    /* warp-stack entries of the packet traversal (from the tree depth) */
+    double beta_repair_leaf; /* far-test factor of the FP64 repair's leaves (0: exact sum over every leaf) */
 } gwn_model_stats;
 
 gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);

@@ -65,7 +65,8 @@ class gwn_model_stats(ctypes.Structure):
                 ("build_ms", ctypes.c_double), ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double),
                 ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double), ("device", ctypes.c_int32),
-                ("bin_points_per_cell", ctypes.c_int32), ("stack_depth", ctypes.c_int32)]
+                ("bin_points_per_cell", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
+                ("beta_repair_leaf", ctypes.c_double)]
 
 
 class gwn_serve_opts(ctypes.Structure):

@@ -416,10 +416,11 @@ constexpr size_t kChunk = (size_t)1 << 19;  // points per pass of the query pipe
 constexpr int kQueryStats = 20;              // entries of gwn_last_query_stats
 
 // beta of the FP64 repair when the build leaves it automatic: the exact sum over
-// every leaf for small models, else the traversal at 3 beta, whose order-2
-// remainder is 3^-4 = 1/81 of the bulk's (Eq. 3's remainder falls like beta^-4)
+// every leaf for small models, else the traversal at (by default) 3 beta, whose
+// order-2 remainder is 3^-4 = 1/81 of the bulk's (Eq. 3's remainder falls like
+// beta^-4); the autotuner may lower the factor (repair_node_factor)
 double auto_beta_repair(const gwn_model_s* m, double beta) {
-    return m->host.n_leaves <= 512 ? 0.0 : 3.0 * beta;
+    return m->host.n_leaves <= 512 ? 0.0 : m->repair_node_factor * beta;
 }
 
 gwn_status ensure_workspace(gwn_model_s* m, size_t n, size_t stage_bytes) {
@@ -464,10 +465,12 @@ static QueryParams query_params(const gwn_model_s* m, const gwn_query_opts& qo, 
     double beta_leaf = qo.beta_leaf > 0 ? qo.beta_leaf : (m->opts.beta_leaf > 0 ? m->opts.beta_leaf : beta);
     p.beta2_leaf = (float)(beta_leaf * beta_leaf);
     double br = m->opts.beta_repair;
-    if (br < 0) br = auto_beta_repair(m, beta);
+    const bool automatic = br < 0;
+    if (automatic) br = auto_beta_repair(m, beta);
     p.beta2_repair = br > 0 ? br * br : 0.0;
-    // the repair's leaves keep the bulk's ratio beta_leaf / beta
-    const double brl = br * beta_leaf / beta;
+    // the repair's leaves: the automatic factor times beta_leaf, or, with a given
+    // beta_repair, the bulk's ratio beta_leaf / beta
+    const double brl = br > 0 ? (automatic ? m->repair_leaf_factor * beta_leaf : br * beta_leaf / beta) : 0.0;
     p.beta2_repair_leaf = brl > 0 ? brl * brl : 0.0;
     p.band = (float)(qo.repair_band > 0 ? qo.repair_band : m->opts.repair_band);
     p.mode = qo.mode;
@@ -733,6 +736,26 @@ __global__ void k_err(int n, const double* a, const double* b, double* out) {
     if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long*>(out), __double_as_longlong(smax[0]));
 }
 
+// max |a - b| over the points whose status carries GWN_QS_REPAIRED, and their count
+__global__ void k_err_repaired(int n, const double* a, const double* b, const uint32_t* st, double* out, int* cnt) {
+    __shared__ double smax[128];
+    double m = 0;
+    int c = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (st[i] & GWN_QS_REPAIRED) {
+            m = fmax(m, fabs(a[i] - b[i]));
+            ++c;
+        }
+    smax[threadIdx.x] = m;
+    atomicAdd(cnt, c);
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long*>(out), __double_as_longlong(smax[0]));
+}
+
 static gwn_status autotune(gwn_model_s* m) {
     const int d = m->dim;
     const HostModel& H = m->host;
@@ -832,10 +855,12 @@ static gwn_status autotune(gwn_model_s* m) {
         }
         if (any_ok && best_b > 0 && b > 2.0 * best_b) break;  // larger beta only costs more
     }
-    cudaFree(ref);
-    cudaFree(w);
-    cudaFree(err);
-    cudaFree(dp);
+    struct Free {
+        std::vector<void*> p;
+        ~Free() {
+            for (void* q : p) cudaFree(q);
+        }
+    } frees{{ref, w, err, dp}};
     if (s != GWN_OK) return s;
     if (best_b == 0) {  // nothing met the tolerance: the most accurate candidate tried
         best_b = fb_b > 0 ? fb_b : 8.0;
@@ -913,6 +938,43 @@ static gwn_status autotune(gwn_model_s* m) {
         cudaFree(dt);
         cudaFree(wt);
         if (!ok) return fail(GWN_ERR_CUDA, "autotune timing failed");
+    }
+    // The automatic FP64 repair (more than 512 leaves): every validation point
+    // whose value is fractional is sent through the repair (band 0.4999), and the
+    // node and leaf factors are lowered from 3 while its values stay within 1e-7
+    // of the FP64 direct sum; fewer FP64 pairs per repaired point.
+    if (d == 3 && m->opts.beta_repair < 0 && H.n_leaves > 512 && m->opts.precision == GWN_PREC_FP32_REPAIR) {
+        const double facs[][2] = {{3.0, 3.0}, {2.5, 2.5}, {2.5, 2.0}, {2.0, 2.0}, {2.0, 1.5}};
+        uint32_t* dst = nullptr;
+        int* dcnt = nullptr;
+        bool ok = cudaMalloc(&dst, nv * sizeof(uint32_t)) == cudaSuccess && cudaMalloc(&dcnt, sizeof(int)) == cudaSuccess;
+        double keep_n = m->repair_node_factor, keep_l = m->repair_leaf_factor;
+        for (const auto& f : facs) {
+            if (!ok) break;
+            m->repair_node_factor = f[0];
+            m->repair_leaf_factor = f[1];
+            gwn_query_opts qr;
+            gwn_default_query_opts(&qr);
+            qr.repair_band = 0.4999;
+            double e = 0;
+            int cnt = 0;
+            ok = gwn_enqueue_device(m, dp, GWN_F32, nv, w, nullptr, dst, qr, 0, m->ws) == GWN_OK &&
+                 cudaMemset(err, 0, sizeof(double)) == cudaSuccess && cudaMemset(dcnt, 0, sizeof(int)) == cudaSuccess;
+            if (ok) k_err_repaired<<<4, 128>>>(nv, ref, w, dst, err, dcnt);
+            ok = ok && cudaMemcpy(&e, err, sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess &&
+                 cudaMemcpy(&cnt, dcnt, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+            if (std::getenv("GWN_AUTOTUNE_VERBOSE"))
+                std::fprintf(stderr, "[gwn autotune] repair factors %.1f / %.1f: max|dGWN| %.3g over %d repaired\n",
+                             f[0], f[1], e, cnt);
+            if (!ok || e > 1e-7) break;
+            keep_n = f[0];
+            keep_l = f[1];
+        }
+        m->repair_node_factor = keep_n;
+        m->repair_leaf_factor = keep_l;
+        if (dst) cudaFree(dst);
+        if (dcnt) cudaFree(dcnt);
+        if (!ok) return fail(GWN_ERR_CUDA, "autotune of the repair failed");
     }
     // the tuning workspace is not the model's: the first query sizes its own
     if (m->ws_mem) {
@@ -1210,7 +1272,7 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
     s->device_bytes = (int64_t)m->device_bytes;
     s->build_ms = m->build_ms;
     s->beta = m->opts.beta;
-    s->beta_repair = m->opts.beta_repair;
+    s->beta_repair = m->opts.beta_repair < 0 ? auto_beta_repair(m, m->opts.beta) : m->opts.beta_repair;
     s->repair_band = m->opts.repair_band;
     s->order = m->opts.order;
     for (int k = 0; k < 3; ++k) {
@@ -1221,6 +1283,12 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
     s->device = m->device;
     s->bin_points_per_cell = m->dim == 3 ? m->bin_ppc : 0;
     s->stack_depth = m->stack_depth;
+    {
+        const double bl = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
+        const double br = s->beta_repair;
+        s->beta_repair_leaf = br > 0 ? (m->opts.beta_repair < 0 ? m->repair_leaf_factor * bl : br * bl / m->opts.beta)
+                                     : 0.0;
+    }
     return GWN_OK;
 }
 
@@ -1259,7 +1327,7 @@ gwn_status gwn_model_tree(gwn_model m, int32_t* child, double* x0, double* r, do
 
 namespace {
 constexpr char kModelMagic[8] = {'G', 'W', 'N', 'M', 'O', 'D', 'E', 'L'};
-constexpr uint32_t kModelVersion = 4;
+constexpr uint32_t kModelVersion = 5;
 
 template <typename V>
 bool write_vec(FILE* f, const std::vector<V>& v) {
@@ -1348,9 +1416,11 @@ gwn_status gwn_model_save(gwn_model m, const char* path) {
     const int32_t hdr[4] = {(int32_t)kModelVersion, m->dim, m->leaf_far, (int32_t)sizeof(gwn_build_opts)};
     const HostModel& H = m->host;
     const int32_t hm[4] = {H.dim, H.n_leaves, H.max_depth, m->bin_ppc};
+    const double rf[2] = {m->repair_node_factor, m->repair_leaf_factor};
     bool ok = std::fwrite(kModelMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               std::fwrite(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
               std::fwrite(&m->opts, sizeof(gwn_build_opts), 1, f) == 1 && std::fwrite(hm, sizeof(hm), 1, f) == 1 &&
+              std::fwrite(rf, sizeof(rf), 1, f) == 1 &&
               std::fwrite(H.lo, sizeof(H.lo), 1, f) == 1 && std::fwrite(H.hi, sizeof(H.hi), 1, f) == 1 &&
               each_array(const_cast<HostModel&>(H), [&](auto& v) { return write_vec(f, v); });
     ok = (std::fclose(f) == 0) && ok;
@@ -1369,11 +1439,13 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
     }
     char magic[8] = {};
     int32_t hdr[4] = {}, hm[4] = {};
+    double rf[2] = {};
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kModelMagic, 8) == 0 &&
               std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == (int32_t)kModelVersion &&
               (hdr[1] == 2 || hdr[1] == 3) && hdr[3] == (int32_t)sizeof(gwn_build_opts) &&
               std::fread(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
               std::fread(&m->opts, sizeof(gwn_build_opts), 1, f) == 1 && std::fread(hm, sizeof(hm), 1, f) == 1 &&
+              std::fread(rf, sizeof(rf), 1, f) == 1 &&
               std::fread(m->host.lo, sizeof(m->host.lo), 1, f) == 1 &&
               std::fread(m->host.hi, sizeof(m->host.hi), 1, f) == 1;
     try {
@@ -1396,7 +1468,9 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         H.n_leaves = hm[1];
         H.max_depth = hm[2];
         m->bin_ppc = hm[3];
-        ok = hm[3] >= 1 && hm[3] <= 4096;
+        m->repair_node_factor = rf[0];
+        m->repair_leaf_factor = rf[1];
+        ok = hm[3] >= 1 && hm[3] <= 4096 && rf[0] >= 1.0 && rf[0] <= 16.0 && rf[1] >= 1.0 && rf[1] <= 16.0;
         // consistency of the arrays the kernels index
         ok = ok && host_model_consistent(H, m->dim);
     }

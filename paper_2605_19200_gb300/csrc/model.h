@@ -25,6 +25,11 @@ struct gwn_model_s {
     // tree depth)
     int bin_ppc = 16;
     int stack_depth = 96;
+    // automatic FP64 repair (beta_repair < 0, more than 512 leaves): its far
+    // tests at these multiples of beta (nodes) and beta_leaf (leaves); the
+    // autotuner lowers them while the repaired values stay within 1e-7
+    double repair_node_factor = 3.0;
+    double repair_leaf_factor = 3.0;
     double build_ms = 0;
     gwn::HostModel host;       // host copy (inspection)
     gwn::DevTree tree{};

@@ -256,7 +256,7 @@ def _split_model_file(data):
     """(header bytes, [(name, count, payload bytes)]) of a model file."""
     import ctypes
     from paper_2605_19200_gb300 import api
-    off = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 16 + 48
+    off = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 16 + 16 + 48
     head, arrays = data[:off], []
     for name, es in _ARRAY_ELEM:
         n = int(np.frombuffer(data[off:off + 8], dtype=np.uint64)[0])

@@ -2,9 +2,10 @@
 // moments, and the boundary curves the near field integrates), written once
 // for the host build (build3d.cpp) and for the device build stage
 // (build_device.cu).  Both compile the same operations in the same order
-// without fused multiply-adds (g++ in ISO C++ mode does not contract; the
-// device file is compiled with -fmad=false), with IEEE division and square
-// root on both sides, so the two stages produce the same bits.
+// without fused multiply-adds (the host files with -ffp-contract=off, which
+// g++ does not default to on aarch64; the device file with -fmad=false), with
+// IEEE division and square root on both sides, so the two stages produce the
+// same bits.
 #pragma once
 
 #include <cmath>
@@ -35,6 +36,16 @@ inline double binom64_host(int n, int k) {
     static const Table table;  // thread-safe one-time initialisation
     return table.T[n][k];
 }
+// The curve routines that pack_curve calls run out of line in device code,
+// each in its own stack frame: inlined, nvcc 13.0 at -O3 gave the working
+// array of bez4_eval the stack slot of pack_curve's composed points X, so the
+// evaluations in curve_min_level overwrote X.
+#if defined(__CUDA_ARCH__)
+#define GWN_OUTLINE __noinline__
+#else
+#define GWN_OUTLINE
+#endif
+
 #if defined(__CUDA_ARCH__)
 #define GWN_BINOM64(n, k) c_binom64[n][k]
 #else
@@ -175,7 +186,7 @@ GWN_HD inline void leaf_moments_core(const Net& net, const TP* bnd, const double
 // Bezier space curve of degree 6 d, exactly,
 //     X(t) = sum_ij C(3,i) C(3,j) U^i (W - U)^(3-i) V^j (W - V)^(3-j) h_ij,
 // X holds (6 d + 1) homogeneous points of 4 doubles.
-GWN_HD inline void compose(const TP& p, const Net& N, double* X) {
+GWN_HD GWN_OUTLINE inline void compose(const TP& p, const Net& N, double* X) {
     int d = p.deg;
     double U[4], V[4], W[4], WU[4], WV[4];
     for (int i = 0; i <= d; ++i) {
@@ -220,7 +231,7 @@ GWN_HD inline void compose(const TP& p, const Net& N, double* X) {
 // homogeneous point and derivative of a degree-D Bezier curve (D + 1 points of
 // 4 doubles in X) at t, by de Casteljau: the two points of the last-but-one
 // level give the derivative D (b1 - b0) and the point (1 - t) b0 + t b1
-GWN_HD inline void bez4_eval(const double* X, int D, double t, double P[4], double dP[4]) {
+GWN_HD GWN_OUTLINE inline void bez4_eval(const double* X, int D, double t, double P[4], double dP[4]) {
     double b[kMaxC3Deg + 1][4];
     for (int i = 0; i <= D; ++i)
         for (int c = 0; c < 4; ++c) b[i][c] = X[i * 4 + c];
@@ -252,7 +263,7 @@ GWN_HD inline void curve_point(const double* X, int D, double t, double x[3], do
 // whose exact integral is the chord x(b) - x(a) -- to 1e-6 of the panel's arc
 // length.  A quarter circle (weights 1, 1/sqrt 2, 1) composed with a bicubic
 // net has its poles at t = 1/2 +- 1.21 i: rho ~ 5 on [0, 1], ~ 10 on its halves.
-GWN_HD inline int curve_min_level(const double* X, int D, const double* x4, const double* w4) {
+GWN_HD GWN_OUTLINE inline int curve_min_level(const double* X, int D, const double* x4, const double* w4) {
     for (int L = 0; L < kMaxMinLevel; ++L) {
         const int np = 1 << L;
         const double h = 1.0 / np;
@@ -284,7 +295,7 @@ GWN_HD inline int curve_min_level(const double* X, int D, const double* x4, cons
 // as the kernels compute it).  A panel below the curve's minimum level gets an
 // infinite length, so the table itself tells the kernel to skip it (level 0)
 // or to leave the curve to the full evaluator (level 1).
-GWN_HD inline void node_table(const double* X, int D, const float cen[3], float mult, int min_level, const double* x4,
+GWN_HD GWN_OUTLINE inline void node_table(const double* X, int D, const float cen[3], float mult, int min_level, const double* x4,
                               float4 out[kC3NodeVec]) {
     const double a0[3] = {0.0, 0.0, 0.5}, hh[3] = {1.0, 0.5, 0.5};
     float len[3];
@@ -320,7 +331,7 @@ GWN_HD inline void node_table(const double* X, int D, const float cen[3], float 
 // absolute positions and tangents at the 8 Gauss-Legendre nodes of the level-0
 // panel and of the two level-1 panels, and the panels' length estimates with
 // the 8-point rule's span factor 1.1 (as the FP64 kernels compute them)
-GWN_HD inline void node_table64(const double* X, int D, double mult, const double* x8, double* out) {
+GWN_HD GWN_OUTLINE inline void node_table64(const double* X, int D, double mult, const double* x8, double* out) {
     const double a0[3] = {0.0, 0.0, 0.5}, hh[3] = {1.0, 0.5, 0.5};
     for (int p = 0; p < 3; ++p) {
         double* nodes = out + 4 + 48 * p;
@@ -342,7 +353,7 @@ GWN_HD inline void node_table64(const double* X, int D, double mult, const doubl
 // (c_{i+1} - c_i), then the same 2 D + 1 points of the reversed curve (read
 // for t > 1/2); pts32 relative to the leaf centre (2 (2 D + 1) float4), pts64
 // absolute (2 (2 D + 1) x 4 doubles)
-GWN_HD inline void curve_points(const double* X, int D, const float cen[3], float4* pts32, double* pts64) {
+GWN_HD GWN_OUTLINE inline void curve_points(const double* X, int D, const float cen[3], float4* pts32, double* pts64) {
     const int n = 2 * D + 1;
     double rel[(kMaxC3Deg + 1) * 4];
     for (int t = 0; t <= D; ++t) {

@@ -59,7 +59,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
                      "-I", INCLUDE, "-c", os.path.join(CSRC, s), "-o", o])
     for s in cpp:
         o = os.path.join(BUILD_DIR, s + ".o")
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-pthread",
+        # no contraction into fused multiply-adds (g++ contracts by default on
+        # aarch64): the host stage of the 3D build must round like the device stage
+        jobs.append(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-I", INCLUDE, "-I", CSRC, "-pthread",
                      "-c", os.path.join(CSRC, s), "-o", o])
 
     def run(cmd):

@@ -36,7 +36,7 @@ def hx():
     os.makedirs(OUT_DIR, exist_ok=True)
     csrc = os.path.join(ROOT, "paper_2605_19200_gb300", "csrc")
     cmd = [nvcc, "-std=c++17", "-O2", "-fmad=false", "-gencode", "arch=compute_103a,code=sm_103a", "-Xcompiler",
-           "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", csrc, SRC, os.path.join(csrc, "build.cpp"),
+           "-fPIC,-ffp-contract=off", "-shared", "-I", os.path.join(ROOT, "include"), "-I", csrc, SRC, os.path.join(csrc, "build.cpp"),
            os.path.join(csrc, "build3d.cpp"), os.path.join(csrc, "build_device.cu"), "-o", LIB]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr

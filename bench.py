@@ -128,9 +128,11 @@ def aggregate_ranks(ms, units_per_rank, world, device):
     return ms, world * units_per_rank / (ms / 1e3)
 
 
-def flops_traversal(w):
+def flops_traversal(w, order3=False):
     # per internal node / leaf visited: far test (10); per Taylor evaluation: 72
-    return 10 * (w["nodes"] + w["leaf_tests"]) + 72 * w["far"]
+    # at order 2, 120 with the order-3 terms (the quadratic and quartic of the
+    # third-order moments)
+    return 10 * (w["nodes"] + w["leaf_tests"]) + (120 if order3 else 72) * w["far"]
 
 
 FAST_NODE_FLOPS = 34    # a node read from a curve's node table: r, |r|, s.r, s x r, the integrand (+ 2 SFU ops)
@@ -345,6 +347,8 @@ def main():
     ap.add_argument("--query-scale", type=float, default=1.0, help="fraction of each model's queries (default 1)")
     ap.add_argument("--beta", type=float, default=BETA)
     ap.add_argument("--beta-leaf", type=float, default=0.0)
+    ap.add_argument("--order", type=int, default=2, choices=[2, 3],
+                    help="Taylor order of the models' build (3: the autotuner picks order 2 or 3 per model)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the single-model configurations 1-3")
     ap.add_argument("--streams", type=int, default=4,
@@ -379,7 +383,7 @@ def main():
     log("workload generated")
     models, points, outs = [], [], []
     for patches, q in workload:
-        m = gwn.gwn_build_3d(patches, beta=args.beta, beta_leaf=args.beta_leaf)
+        m = gwn.gwn_build_3d(patches, beta=args.beta, beta_leaf=args.beta_leaf, order=args.order)
         models.append(m)
         pt = torch.from_numpy(q.astype(np.float32)).to(dev)
         points.append(pt)
@@ -393,6 +397,7 @@ def main():
     tuned = [(round(m.info()["beta"], 2), round(m.info()["beta_leaf"], 2)) for m in models]
     knobs = [(m.info()["bin_points_per_cell"], m.info()["stack_depth"]) for m in models]
     repair_betas = [(round(m.info()["beta_repair"], 2), round(m.info()["beta_repair_leaf"], 2)) for m in models]
+    eval_orders = [m.info()["eval_order"] for m in models]
     n_leaves = sum(m.info()["n_leaves"] for m in models)
     n_patches = sum(len(p) for p, _ in workload)
     stream = torch.cuda.current_stream(dev)
@@ -455,7 +460,7 @@ def main():
         us["k_pair_eval"] += s["full_us"]
         m.query(p, out=o, stream=stream, count_work=True)
         w = m.last_query_stats()
-        fl["k_trav3"] += flops_traversal(w)
+        fl["k_trav3"] += flops_traversal(w, m.info()["eval_order"] >= 3)
         fl["k_pair_fast"] += FAST_NODE_FLOPS * w["fast_nodes"]
         fl["k_pair_eval"] += flops_leaves(w) - FAST_NODE_FLOPS * w["fast_nodes"]
         repaired += w["repaired"]
@@ -609,7 +614,8 @@ def main():
                    "beta": "autotuned" if args.beta == 0 else args.beta, "beta_per_model": tuned,
                    "bin_points_per_cell_stack_depth_per_model": knobs,
                    "repair_beta_per_model": repair_betas,
-                   "tolerance": 1e-4, "order": 2, "precision": "fp32 bulk + fp64 repair",
+                   "tolerance": 1e-4, "order": args.order, "eval_order_per_model": eval_orders,
+                   "precision": "fp32 bulk + fp64 repair",
                    "l2": f"inputs larger than L2 ({total_q * 12 / 1e6:.0f} MB of points per step)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1),
                    "launch": (f"gwn_query_batch: one CUDA graph launch per step over {args.streams} streams"

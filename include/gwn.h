@@ -7,7 +7,8 @@
  * (Algorithm 1): adaptive subdivision (Section 3.2), uncentred moments summed
  * up a Karras LBVH and centred in place (Section 3.1, Eq. 3 and the moment
  * transform), and a per-query traversal that evaluates the order-0/1/2 Taylor
- * expansion of Eq. 3 for clusters that pass the far test of Section 3 and the
+ * expansion of Eq. 3 (order 3 in 3D as an extension) for clusters that pass
+ * the far test of Section 3 and the
  * exact GWN (Section 3.3) for the leaves it reaches.
  *
  * Conventions shared by every call
@@ -100,7 +101,10 @@ enum {
 typedef struct {
     double tolerance;     /* target max |dGWN| for the FP32 path (default 1e-4) */
     double max_aabb_frac; /* subdivide until a leaf's box diagonal < frac * shape diagonal (0.1); <= 0: no subdivision */
-    int32_t order;        /* Taylor order 0, 1 or 2 (default 2) */
+    int32_t order;        /* Taylor order 0, 1 or 2 of Eq. 3 (default 2); 3D models also take 3, the next
+                             term of the same expansion (third-order moments int y y y n), beyond the
+                             paper: its remainder falls one power of r/|x0 - q| faster, so the same
+                             tolerance holds at a smaller beta and beta_leaf */
     double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2, or 0 = autotune:
                              among the (beta, beta_leaf) pairs whose FP32 error on validation points
                              (FP64 direct sum on the device) stays below tolerance / 2, the fastest on
@@ -226,6 +230,8 @@ typedef struct {
                                2D: 0 (9 bits per axis) */
     int32_t stack_depth;    /* warp-stack entries of the packet traversal (from the tree depth) */
     double beta_repair_leaf; /* far-test factor of the FP64 repair's leaves (0: exact sum over every leaf) */
+    int32_t eval_order;     /* Taylor order the queries evaluate: `order`, or 2 for a 3D model built with
+                               order 3 whose autotuner found order 2 faster at the tolerance */
 } gwn_model_stats;
 
 gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
@@ -257,9 +263,10 @@ gwn_status gwn_model_leaves(gwn_model model, int64_t* prim, double* param);
 
 /* Copy the FP64 tree to host memory (used by the tests): for internal node k,
  * child[2k], child[2k+1] (>= 0: internal node, < 0: leaf ~index), centroid
- * x0[dim k ..], radius r[k], and the centred moments mom[k * M ..] with
- * M = d + d^2 + d^3 laid out as m0[d], m1[d][d], m2[d][d][d] with
- * m1_ij = int (x - x0)_i n_j and m2_ijk = int (x - x0)_i (x - x0)_j n_k.
+ * x0[dim k ..], radius r[k], and the centred moments mom[k * M ..] laid out as
+ * m0[d], m1[d][d], m2[d][d][d] with m1_ij = int (x - x0)_i n_j and
+ * m2_ijk = int (x - x0)_i (x - x0)_j n_k (M = 14 in 2D), followed in 3D by
+ * m3[3][3][3][3], m3_ijlk = int (x - x0)_i (x - x0)_j (x - x0)_l n_k (M = 120).
  * Any pointer may be NULL. */
 gwn_status gwn_model_tree(gwn_model model, int32_t* child, double* x0, double* r, double* mom);
 

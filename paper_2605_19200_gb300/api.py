@@ -66,7 +66,7 @@ class gwn_model_stats(ctypes.Structure):
                 ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double), ("device", ctypes.c_int32),
                 ("bin_points_per_cell", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
-                ("beta_repair_leaf", ctypes.c_double)]
+                ("beta_repair_leaf", ctypes.c_double), ("eval_order", ctypes.c_int32)]
 
 
 class gwn_serve_opts(ctypes.Structure):
@@ -236,7 +236,7 @@ class Model:
     def tree(self):
         info = self.info()
         ni, d = info["n_nodes"], self.dim
-        M = d + d * d + d ** 3
+        M = 14 if d == 2 else 120   # orders 0-2 in 2D, 0-3 in 3D
         child = np.zeros((max(ni, 1), 2), dtype=np.int32)
         x0 = np.zeros((max(ni, 1), d))
         r = np.zeros(max(ni, 1))

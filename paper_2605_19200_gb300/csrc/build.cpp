@@ -127,7 +127,8 @@ struct Karras {
 };
 }  // namespace
 
-static int momn(int d) { return d + d * d + d * d * d; }
+// uncentred moments per leaf or node: orders 0-2 in 2D, 0-3 in 3D
+static int momn(int d) { return d == 2 ? 2 + 4 + 8 : kLeafMom3; }
 
 // Folded polynomial coefficients of the order-`order` Taylor expansion (Eq. 3)
 // for moments centred at x0, as evaluated by the kernels.
@@ -206,6 +207,53 @@ static void fold_moments_3d(const double* m, int order, double* f) {
         f[21] = e * S3(1, 2, 2);
         f[22] = e * S3(0, 1, 2);
     }
+    if (order >= 3) {
+        // The order-3 term (1/6) sum d_i d_j d_l K_k(r) M3_ijlk of the same
+        // expansion, K(v) = v / |v|^3, M3_ijlk = int y_i y_j y_l n_k.  With
+        // d_ijl K_k = -3 (d_jk d_il + d_ij d_kl + d_ik d_jl) / |r|^5
+        //             + 15 (d_jk r_i r_l + d_ij r_k r_l + d_ik r_j r_l
+        //                   + d_il r_j r_k + d_jl r_i r_k + d_kl r_i r_j) / |r|^7
+        //             - 105 r_i r_j r_l r_k / |r|^9
+        // and M3 symmetric in its first three indices it is
+        //   -1.5 T / |r|^5 + 7.5 r^T (Q + R) r / |r|^7 - 17.5 M3[r r r r] / |r|^9,
+        // T = sum_ik M3_iikk, Q_ab = sum_j M3_abjj, R_lk = sum_i M3_iilk.
+        const double* m3 = m + 39;  // m3[((i*3 + j)*3 + l)*3 + k]
+        auto M3 = [&](int i, int j, int l, int k) { return m3[((i * 3 + j) * 3 + l) * 3 + k]; };
+        auto S4 = [&](int i, int j, int l, int k) {
+            int idx[4] = {i, j, l, k};
+            std::sort(idx, idx + 4);
+            double s = 0;
+            do { s += M3(idx[0], idx[1], idx[2], idx[3]); } while (std::next_permutation(idx, idx + 4));
+            return s;
+        };
+        double T = 0, P[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) T += M3(i, i, k, k);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double q = 0, r = 0;
+                for (int j = 0; j < 3; ++j) {
+                    q += M3(a, b, j, j);
+                    r += M3(j, j, a, b);
+                }
+                P[a][b] = q + r;
+            }
+        f[23] = -1.5 * c * T;
+        const double g = 7.5 * c;
+        f[24] = g * P[0][0];
+        f[25] = g * P[1][1];
+        f[26] = g * P[2][2];
+        f[27] = g * (P[0][1] + P[1][0]);
+        f[28] = g * (P[0][2] + P[2][0]);
+        f[29] = g * (P[1][2] + P[2][1]);
+        // quartic monomials in the kernels' grouping: x^2 (x^2 xy xz y^2 z^2 yz),
+        // y^2 (y^2 xy yz z^2 xz), z^2 (z^2 xz yz xy)
+        const int quart[15][4] = {{0, 0, 0, 0}, {0, 0, 0, 1}, {0, 0, 0, 2}, {0, 0, 1, 1}, {0, 0, 2, 2},
+                                  {0, 0, 1, 2}, {1, 1, 1, 1}, {0, 1, 1, 1}, {1, 1, 1, 2}, {1, 1, 2, 2},
+                                  {0, 1, 1, 2}, {2, 2, 2, 2}, {0, 2, 2, 2}, {1, 2, 2, 2}, {0, 1, 2, 2}};
+        const double h = -17.5 * c;
+        for (int k = 0; k < 15; ++k) f[30 + k] = h * S4(quart[k][0], quart[k][1], quart[k][2], quart[k][3]);
+    }
 }
 
 // Centroid (weighted, or the box centre when the weight is zero), radius (half
@@ -214,7 +262,8 @@ static void fold_moments_3d(const double* m, int order, double* f) {
 //   int (x - x0) n         = int x n - x0 (x) int n
 //   int (x - x0)(x - x0) n = int x x n - x0 (x) int x n - (int x n with x0 in the
 //                            second slot) + x0 (x) x0 (x) int n,
-// with the uncentred moments m taken about the reference point xref.
+// in 3D also the third-order moments by the same binomial expansion, with the
+// uncentred moments m taken about the reference point xref.
 static void centre_block(int d, const double* box, double w, const double* wx, const double* m, const double* xref,
                          double* x0, double* radius, double* c) {
     double rr = 0;
@@ -240,6 +289,22 @@ static void centre_block(int d, const double* box, double w, const double* wx, c
             for (int k = 0; k < d; ++k)
                 c2[(i * d + j) * d + k] =
                     m2[(i * d + j) * d + k] - y[i] * m1[j * d + k] - y[j] * m1[i * d + k] + y[i] * y[j] * m0[k];
+    if (d == 3) {
+        // int (x - x0)_i (x - x0)_j (x - x0)_l n_k from the uncentred moments
+        const double* m3 = m + 39;
+        double* c3 = c + 39;
+        auto M2 = [&](int a, int b, int k) { return m2[(a * 3 + b) * 3 + k]; };
+        auto M1 = [&](int a, int k) { return m1[a * 3 + k]; };
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l)
+                    for (int k = 0; k < 3; ++k) {
+                        const int o = ((i * 3 + j) * 3 + l) * 3 + k;
+                        c3[o] = m3[o] - y[i] * M2(j, l, k) - y[j] * M2(i, l, k) - y[l] * M2(i, j, k) +
+                                y[i] * y[j] * M1(l, k) + y[i] * y[l] * M1(j, k) + y[j] * y[l] * M1(i, k) -
+                                y[i] * y[j] * y[l] * m0[k];
+                    }
+    }
 }
 
 void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm, int adaptive_beta) {

@@ -224,7 +224,7 @@ struct Leaf {
     std::vector<TP> bnd; // visible boundary in local coordinates
     std::vector<double> mult;
     double lo[3], hi[3];
-    double mom[39];      // uncentred moments about xref
+    double mom[kLeafMom3];  // uncentred moments about xref (orders 0-3)
     double area, ax[3];  // int |n|, int x |n| (absolute x)
     double nrm[3];
 };
@@ -661,7 +661,7 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
         }
         for (int i = 0; i < nl; ++i) {
             Leaf& L = leaves[i];
-            std::memcpy(L.mom, &mom[(size_t)i * 39], sizeof(L.mom));
+            std::memcpy(L.mom, &mom[(size_t)i * kLeafMom3], sizeof(L.mom));
             L.area = area_ax[(size_t)i * 4];
             for (int k = 0; k < 3; ++k) L.ax[k] = area_ax[(size_t)i * 4 + 1 + k];
         }
@@ -670,7 +670,7 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
     S.dim = 3;
     std::memcpy(S.xref, xref, sizeof(xref));
     S.box.resize((size_t)nl * 6);
-    S.mom.resize((size_t)nl * 39);
+    S.mom.resize((size_t)nl * kLeafMom3);
     S.wsum.resize(nl);
     S.wx.resize((size_t)nl * 3);
     for (int i = 0; i < nl; ++i) {
@@ -680,7 +680,7 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
             S.box[i * 6 + 3 + k] = L.hi[k];
             S.wx[i * 3 + k] = L.ax[k];
         }
-        std::memcpy(&S.mom[(size_t)i * 39], L.mom, sizeof(L.mom));
+        std::memcpy(&S.mom[(size_t)i * kLeafMom3], L.mom, sizeof(L.mom));
         S.wsum[i] = L.area;
     }
     std::vector<int> perm;

@@ -52,7 +52,7 @@ __global__ void k_leaf_moments(int nl, const Net* nets, const TP* pieces, const 
     const double xr[3] = {xref.x, xref.y, xref.z};
     double area, ax[3];
     leaf_moments_core(nets[i], pieces + off[i], mult + off[i], off[i + 1] - off[i], xr, rule.x, rule.w, rule.n,
-                      mom + (size_t)i * 39, &area, ax);
+                      mom + (size_t)i * kLeafMom3, &area, ax);
     area_ax[(size_t)i * 4] = area;
     for (int k = 0; k < 3; ++k) area_ax[(size_t)i * 4 + 1 + k] = ax[k];
 }
@@ -96,7 +96,7 @@ std::string device_leaf_moments(const std::vector<Net>& nets, const std::vector<
         rule.x[k] = gx[k];
         rule.w[k] = gw[k];
     }
-    mom->assign((size_t)nl * 39, 0.0);
+    mom->assign((size_t)nl * kLeafMom3, 0.0);
     area_ax->assign((size_t)nl * 4, 0.0);
     if (nl == 0) return "";
     if (!ensure_binomials()) return cuda_msg("binomial table");

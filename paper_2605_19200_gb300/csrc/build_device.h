@@ -14,7 +14,7 @@ namespace gwn {
 
 // Leaf moments (leaf_moments_core) of nl leaves: nets[i], the pieces
 // [off[i], off[i + 1]) of `pieces` with multiplicities `mult`, the n-point
-// rule (gx, gw).  mom receives 39 doubles per leaf, area_ax 4 (area, ax).
+// rule (gx, gw).  mom receives kLeafMom3 (120) doubles per leaf, area_ax 4 (area, ax).
 // Runs on the current CUDA device; returns "" or an error message.
 std::string device_leaf_moments(const std::vector<Net>& nets, const std::vector<TP>& pieces,
                                 const std::vector<double>& mult, const std::vector<int>& off, const double* xref,

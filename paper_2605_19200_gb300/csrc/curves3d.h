@@ -143,12 +143,13 @@ GWN_HD inline void net_eval(const Net& N, double u, double v, double* S, double*
 // Leaf moments by Green's theorem on the leaf's local boundary (Section 3.1):
 // int_D f du dv = oint F dv with F(u, v) = int_0^u f(s, v) ds, both integrals
 // with the n-point Gauss-Legendre rule (gx, gw on [0, 1]).  mom receives the
-// uncentred moments about xref, int n (3), int x n (9), int x x n (27); area =
-// int |n|, ax = int x |n| (absolute x).
+// uncentred moments about xref, int n (3), int x n (9), int x x n (27) and
+// int x x x n (81, for the order-3 far field); area = int |n|, ax = int x |n|
+// (absolute x).
 GWN_HD inline void leaf_moments_core(const Net& net, const TP* bnd, const double* mult, int nb, const double* xref,
                                      const double* gx, const double* gw, int n, double* mom, double* area,
                                      double* ax) {
-    for (int k = 0; k < 39; ++k) mom[k] = 0.0;
+    for (int k = 0; k < kLeafMom3; ++k) mom[k] = 0.0;
     *area = 0;
     ax[0] = ax[1] = ax[2] = 0;
     for (int pi = 0; pi < nb; ++pi) {
@@ -174,6 +175,10 @@ GWN_HD inline void leaf_moments_core(const Net& net, const TP* bnd, const double
                     for (int j = 0; j < 3; ++j) {
                         double xx = wt * x[i] * x[j];
                         for (int k = 0; k < 3; ++k) mom[12 + (i * 3 + j) * 3 + k] += xx * N[k];
+                        for (int l = 0; l < 3; ++l) {
+                            double xxx = xx * x[l];
+                            for (int k = 0; k < 3; ++k) mom[39 + ((i * 3 + j) * 3 + l) * 3 + k] += xxx * N[k];
+                        }
                     }
                 *area += wt * nl;
                 for (int k = 0; k < 3; ++k) ax[k] += wt * nl * S[k];

@@ -180,6 +180,7 @@ gwn_status upload_model(gwn_model_s* m) {
     gwn_status s;
 #define UP(vec, field) if ((s = upload(m, H.vec, &t.field)) != GWN_OK) return s
     t.leaf_far = m->leaf_far;
+    t.order3 = H.dim == 3 && m->eval_order >= 3 ? 1 : 0;
     UP(lhdr, lhdr);
     UP(lmom, lmom);
     UP(lhdr64, lhdr64);
@@ -222,10 +223,11 @@ gwn_status finish_build(gwn_model_s* m, gwn_model* out) {
     return GWN_OK;
 }
 
-gwn_status check_opts(const gwn_build_opts& o) {
+gwn_status check_opts(const gwn_build_opts& o, int dim) {
     if (!(o.beta == 0.0 || o.beta >= 2.0) || !std::isfinite(o.beta)) return fail(GWN_ERR_INVALID_ARG, "beta must be 0 (autotune) or >= 2");
     if (!(o.beta_leaf == 0.0 || o.beta_leaf >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_leaf must be 0 or >= 2");
-    if (o.order < 0 || o.order > 2) return fail(GWN_ERR_INVALID_ARG, "order must be 0, 1 or 2");
+    if (o.order < 0 || o.order > (dim == 3 ? 3 : 2))
+        return fail(GWN_ERR_INVALID_ARG, dim == 3 ? "order must be 0, 1, 2 or 3" : "order must be 0, 1 or 2");
     if (o.adaptive_beta != 0 && o.adaptive_beta != 1) return fail(GWN_ERR_INVALID_ARG, "adaptive_beta must be 0 or 1");
     if (o.device_build < -1 || o.device_build > 1) return fail(GWN_ERR_INVALID_ARG, "device_build must be -1, 0 or 1");
     if (!(o.beta_repair <= 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be <= 0 or >= 2");
@@ -717,11 +719,13 @@ void gwn_default_query_opts(gwn_query_opts* q) {
 // ---------------------------------------------------------------- autotuner
 //
 // Picks the far-field factors (beta for internal nodes, beta_leaf for 3D
-// leaves) of a model: validation points -- uniform in the model's box, plus
-// points a little off the surface at random leaf centroids -- are evaluated
-// exactly (FP64 direct sum on the device), then with the FP32 path for every
-// candidate pair.  Among the pairs whose max |dGWN| stays below half the
-// tolerance, the one with the smallest counted work (flops per point) wins.
+// leaves) of a model, and for a 3D model built with order 3 the Taylor order
+// the queries evaluate (3, or 2 from the same coefficients): validation points
+// -- uniform in the model's box, plus points a little off the surface at
+// random leaf centroids -- are evaluated exactly (FP64 direct sum on the
+// device), then with the FP32 path for every candidate.  The candidates whose
+// max |dGWN| stays below half the tolerance are ranked by counted work (flops
+// per point) and the cheapest few of each order are timed (below).
 
 __global__ void k_err(int n, const double* a, const double* b, double* out) {
     __shared__ double smax[128];
@@ -795,14 +799,20 @@ static gwn_status autotune(gwn_model_s* m) {
     qo.mode = GWN_MODE_DIRECT;
     qo.precision = GWN_PREC_FP64;
     if (s == GWN_OK) s = gwn_enqueue_device(m, dp, GWN_F32, nv, ref, nullptr, nullptr, qo, 0, m->ws);
-    const double betas[] = {3.0, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0};
+    const double betas[] = {3.0, 3.5, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0};
     // 2D leaves have no separate factor (0 = beta); 3D leaves: per-level factors
-    const double leafb[] = {0.0, 2.0, 2.5, 3.0, 4.0, 5.0};
+    const double leafb[] = {0.0, 2.0, 2.5, 3.0, 3.5, 4.0, 5.0};
     double best_cost = 1e300, best_b = 0, best_bl = 0;
-    std::vector<std::tuple<double, double, double>> ok_cands;  // (counted flops, beta, beta_leaf)
+    int best_o = m->eval_order;
+    std::vector<std::tuple<double, double, double, int>> ok_cands;  // (counted flops, beta, beta_leaf, order)
     double fb_err = 1e300, fb_b = 0, fb_bl = 0;  // fallback: smallest error seen
+    int fb_o = m->eval_order;
     const double tol = 0.5 * m->opts.tolerance;
+    std::vector<int> orders{m->eval_order};
+    if (d == 3 && m->opts.order >= 3) orders = {3, 2};
+    for (int ord : orders)
     for (double b : betas) {
+        m->tree.order3 = ord >= 3 ? 1 : 0;
         bool any_ok = false;
         for (double bl : leafb) {
             if (s != GWN_OK) break;
@@ -835,25 +845,28 @@ static gwn_status autotune(gwn_model_s* m) {
                 fb_err = e;
                 fb_b = b;
                 fb_bl = blv;
+                fb_o = ord;
             }
-            double cost = 10.0 * (wk[kWorkNodes] + wk[kWorkLeafTests]) + 72.0 * wk[kWorkFar] +
+            double cost = 10.0 * (wk[kWorkNodes] + wk[kWorkLeafTests]) + (ord >= 3 ? 120.0 : 72.0) * wk[kWorkFar] +
                           28.0 * wk[kWorkGlDeg] + 70.0 * wk[kWorkGlNodes] + 2000.0 * wk[kWorkHits] +
                           kFastNodeFlops * wk[kWorkFastNodes] +
                           (d == 2 ? 60.0 * wk[kWorkLeaves] : 30.0 * wk[kWorkLeaves]);
             if (std::getenv("GWN_AUTOTUNE_VERBOSE"))
-                std::fprintf(stderr, "[gwn autotune] leaves=%d beta=%.1f beta_leaf=%.1f max|dGWN|=%.3g flops/pt=%.3g\n",
-                             H.n_leaves, b, blv, e, cost / nv);
+                std::fprintf(stderr,
+                             "[gwn autotune] leaves=%d order=%d beta=%.1f beta_leaf=%.1f max|dGWN|=%.3g flops/pt=%.3g\n",
+                             H.n_leaves, ord, b, blv, e, cost / nv);
             if (e <= tol) {
                 any_ok = true;
-                ok_cands.push_back({cost, b, blv});
+                ok_cands.push_back({cost, b, blv, ord});
                 if (cost < best_cost) {
                     best_cost = cost;
                     best_b = b;
                     best_bl = blv;
+                    best_o = ord;
                 }
             }
         }
-        if (any_ok && best_b > 0 && b > 2.0 * best_b) break;  // larger beta only costs more
+        if (any_ok && b >= 8.0) break;  // larger beta only costs more
     }
     struct Free {
         std::vector<void*> p;
@@ -865,18 +878,28 @@ static gwn_status autotune(gwn_model_s* m) {
     if (best_b == 0) {  // nothing met the tolerance: the most accurate candidate tried
         best_b = fb_b > 0 ? fb_b : 8.0;
         best_bl = fb_b > 0 ? fb_bl : 8.0;
+        best_o = fb_o;
     }
     m->opts.beta = best_b;
     m->opts.beta_leaf = d == 3 ? best_bl : 0.0;
+    m->eval_order = best_o;
+    m->tree.order3 = d == 3 && best_o >= 3 ? 1 : 0;
     // Counted flops do not weigh the kernels alike (the traversal's far tests and
     // Taylor terms issue about twice the instructions per counted flop of the
     // node-table leaves), so among the accurate candidates the cheapest four by
-    // count are timed on a uniform sample of the model's box, and the fastest
-    // is kept; then the binning's target points per cell is timed the same way
-    // (the sample is binned at the resolution its size gives, as a query is).
+    // count of each order are timed on a uniform sample of the model's box, and
+    // the fastest is kept; then the binning's target points per cell is timed
+    // the same way (the sample is binned at the resolution its size gives, as a
+    // query is).
     if (ok_cands.size() > 1 || d == 3) {
         std::sort(ok_cands.begin(), ok_cands.end());
-        if (ok_cands.size() > 4) ok_cands.resize(4);
+        {
+            std::vector<std::tuple<double, double, double, int>> keep;
+            int per_order[4] = {0, 0, 0, 0};
+            for (const auto& c : ok_cands)
+                if (per_order[std::get<3>(c)]++ < 4) keep.push_back(c);
+            ok_cands.swap(keep);
+        }
         const int nt = 1 << 16;
         std::vector<float> tp((size_t)nt * d);
         for (int i = 0; i < nt; ++i)
@@ -908,16 +931,19 @@ static gwn_status autotune(gwn_model_s* m) {
         double best_t = 1e300;
         if (ok_cands.size() > 1) {
             for (const auto& c : ok_cands) {
+                m->tree.order3 = d == 3 && std::get<3>(c) >= 3 ? 1 : 0;
                 const double tus = timed(std::get<1>(c), std::get<2>(c));
                 if (std::getenv("GWN_AUTOTUNE_VERBOSE"))
-                    std::fprintf(stderr, "[gwn autotune] beta=%.1f beta_leaf=%.1f: %.1f us for %d points\n",
-                                 std::get<1>(c), std::get<2>(c), tus, nt);
+                    std::fprintf(stderr, "[gwn autotune] order=%d beta=%.1f beta_leaf=%.1f: %.1f us for %d points\n",
+                                 std::get<3>(c), std::get<1>(c), std::get<2>(c), tus, nt);
                 if (ok && tus < best_t) {
                     best_t = tus;
                     m->opts.beta = std::get<1>(c);
                     m->opts.beta_leaf = d == 3 ? std::get<2>(c) : 0.0;
+                    m->eval_order = std::get<3>(c);
                 }
             }
+            m->tree.order3 = d == 3 && m->eval_order >= 3 ? 1 : 0;
         }
         if (d == 3 && ok) {
             const double bl = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
@@ -992,13 +1018,14 @@ static gwn_status build_common(int dim, const void* prims, size_t n, const gwn_b
     gwn_build_opts o;
     gwn_default_build_opts(&o);
     if (opts) o = *opts;
-    gwn_status s = check_opts(o);
+    gwn_status s = check_opts(o, dim);
     if (s != GWN_OK) return s;
     auto t0 = std::chrono::steady_clock::now();
     gwn_model_s* m = new (std::nothrow) gwn_model_s();
     if (!m) return fail(GWN_ERR_OOM, "host allocation failed");
     m->dim = dim;
     m->opts = o;
+    m->eval_order = o.order;
     m->leaf_far = o.leaf_far < 0 ? (dim == 3 ? 1 : 0) : (o.leaf_far ? 1 : 0);
     m->n_primitives = (int64_t)n;
     gwn_status code = GWN_OK;
@@ -1275,6 +1302,7 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
     s->beta_repair = m->opts.beta_repair < 0 ? auto_beta_repair(m, m->opts.beta) : m->opts.beta_repair;
     s->repair_band = m->opts.repair_band;
     s->order = m->opts.order;
+    s->eval_order = m->eval_order;
     for (int k = 0; k < 3; ++k) {
         s->lo[k] = m->host.lo[k];
         s->hi[k] = m->host.hi[k];
@@ -1327,7 +1355,7 @@ gwn_status gwn_model_tree(gwn_model m, int32_t* child, double* x0, double* r, do
 
 namespace {
 constexpr char kModelMagic[8] = {'G', 'W', 'N', 'M', 'O', 'D', 'E', 'L'};
-constexpr uint32_t kModelVersion = 5;
+constexpr uint32_t kModelVersion = 6;
 
 template <typename V>
 bool write_vec(FILE* f, const std::vector<V>& v) {
@@ -1357,7 +1385,7 @@ bool host_model_consistent(const HostModel& H, int dim) {
     if (H.dim != dim || H.n_leaves < 1) return false;
     const size_t nl = (size_t)H.n_leaves, ni = nl - 1, d = (size_t)dim;
     const size_t fv = dim == 2 ? kMom2Vec : kMom3Vec, ff = dim == 2 ? kMom2F64 : kMom3F64;
-    const size_t M = d + d * d + d * d * d;
+    const size_t M = dim == 2 ? 2 + 4 + 8 : kLeafMom3;
     if (H.child.size() != ni || H.hdr.size() != ni || H.mom.size() != ni * fv || H.hdr64.size() != ni * 4 ||
         H.mom64.size() != ni * ff || H.lhdr.size() != nl || H.lmom.size() != nl * fv || H.lhdr64.size() != nl * 4 ||
         H.lmom64.size() != nl * ff || H.x0.size() != ni * d || H.r.size() != ni || H.mom_c.size() != ni * M ||
@@ -1415,7 +1443,7 @@ gwn_status gwn_model_save(gwn_model m, const char* path) {
     if (!f) return fail(GWN_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
     const int32_t hdr[4] = {(int32_t)kModelVersion, m->dim, m->leaf_far, (int32_t)sizeof(gwn_build_opts)};
     const HostModel& H = m->host;
-    const int32_t hm[4] = {H.dim, H.n_leaves, H.max_depth, m->bin_ppc};
+    const int32_t hm[5] = {H.dim, H.n_leaves, H.max_depth, m->bin_ppc, m->eval_order};
     const double rf[2] = {m->repair_node_factor, m->repair_leaf_factor};
     bool ok = std::fwrite(kModelMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               std::fwrite(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
@@ -1438,7 +1466,7 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         return fail(GWN_ERR_OOM, "host allocation failed");
     }
     char magic[8] = {};
-    int32_t hdr[4] = {}, hm[4] = {};
+    int32_t hdr[4] = {}, hm[5] = {};
     double rf[2] = {};
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kModelMagic, 8) == 0 &&
               std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == (int32_t)kModelVersion &&
@@ -1468,13 +1496,15 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         H.n_leaves = hm[1];
         H.max_depth = hm[2];
         m->bin_ppc = hm[3];
+        m->eval_order = hm[4];
         m->repair_node_factor = rf[0];
         m->repair_leaf_factor = rf[1];
-        ok = hm[3] >= 1 && hm[3] <= 4096 && rf[0] >= 1.0 && rf[0] <= 16.0 && rf[1] >= 1.0 && rf[1] <= 16.0;
+        ok = hm[3] >= 1 && hm[3] <= 4096 && rf[0] >= 1.0 && rf[0] <= 16.0 && rf[1] >= 1.0 && rf[1] <= 16.0 &&
+             hm[4] >= 0 && hm[4] <= m->opts.order;
         // consistency of the arrays the kernels index
         ok = ok && host_model_consistent(H, m->dim);
     }
-    if (!ok || check_opts(m->opts) != GWN_OK) {
+    if (!ok || check_opts(m->opts, m->dim) != GWN_OK) {
         delete m;
         return fail(GWN_ERR_INVALID_ARG, std::string("not a model file of this library version: ") + path);
     }

@@ -3,14 +3,16 @@
 // A model is a Karras LBVH (Section 3.1) over leaf primitives.  Internal node k
 // (0 <= k < n_leaves - 1) stores its centroid x0 and squared radius r^2 (radius
 // = half the diagonal of the node's control-point box, Section 3), its two
-// children (>= 0: internal node, < 0: leaf ~i), and the order-2 Taylor
-// coefficients of Eq. 3 folded into the polynomial form evaluated by the
-// kernels (see fold_moments_2d / fold_moments_3d in build.cpp):
+// children (>= 0: internal node, < 0: leaf ~i), and the Taylor coefficients
+// of Eq. 3 (order 2; order 3 in 3D as an extension) folded into the polynomial
+// form evaluated by the kernels (see fold_moments_2d / fold_moments_3d in
+// build.cpp):
 //
 //   2D  w = i2 (A0.r + a1 + i2 (r^T B r + c.r + i2 D[r r r])),  i2 = 1/|r|^2
-//   3D  w = i3 (A0.r + a1 + i2 (r^T B r + c.r + i2 D[r r r])),  i3 = 1/|r|^3
+//   3D  w = i3 (A0.r + a1 + i2 (r^T B r + c.r + e + i2 (D[r r r] + r^T F r
+//                + i2 G[r r r r]))),                             i3 = 1/|r|^3
 //
-// with r = x0 - q.  Every array is a structure of arrays indexed by node or
+// with r = x0 - q (e, F, G: the order-3 terms, zero below order 3).  Every array is a structure of arrays indexed by node or
 // leaf so that a node visit reads one 16-byte header, and the moment block is
 // read only when the far test passes.
 #pragma once
@@ -40,9 +42,10 @@ struct alignas(8) int2 { int x, y; };
 namespace gwn {
 
 constexpr int kMom2Vec = 3;    // float4 per 2D moment block (12 floats)
-constexpr int kMom3Vec = 6;    // float4 per 3D moment block (23 floats + pad)
+constexpr int kMom3Vec = 12;   // float4 per 3D moment block (45 floats + pad; the first 6 hold order <= 2)
 constexpr int kMom2F64 = 12;   // doubles per 2D moment block
-constexpr int kMom3F64 = 24;   // doubles per 3D moment block
+constexpr int kMom3F64 = 48;   // doubles per 3D moment block
+constexpr int kLeafMom3 = 120; // uncentred 3D moments of a leaf: 3 + 9 + 27 + 81
 // 2D leaf: cubic rational Bezier stored as a centre c (float) plus offsets of
 // the control points from c, so that near queries lose no precision to the
 // absolute magnitude of the coordinates:
@@ -114,6 +117,7 @@ struct DevTree {
     int n_internal;
     int root;                  // 0, or ~0 when the model has a single leaf
     int leaf_far;              // 1: leaves also take the far test (their own moments)
+    int order3;                // 1: 3D moment blocks carry the order-3 terms (kMom3Vec float4 read)
     // per-leaf far-field data (same layout as the nodes)
     const float4* lhdr;
     const float4* lmom;

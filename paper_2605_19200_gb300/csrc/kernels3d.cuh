@@ -892,8 +892,22 @@ __device__ inline bool leaf3_warp64(const DevTree& t, int li, const double q[3],
 }
 #endif
 
+// The order-3 part of a folded moment block (f[23 .. 44], zero below order 3):
+// i3 i2 (e + i2 (r^T F r + i2 G[r r r r])), the constant e, the quadratic F and
+// the quartic G of the expansion's third-order term, given r, its squares and
+// the inverse powers i2 = 1/|r|^2, i3 = 1/|r|^3.
 template <typename T>
-GWN_HD inline T far3_eval(const T* f, T rx, T ry, T rz) {
+GWN_HD inline T far3_order3(const T* f, T rx, T ry, T rz, T xx, T yy, T zz, T i2, T i3) {
+    const T xy = rx * ry, xz = rx * rz, yz = ry * rz;
+    const T q = f[24] * xx + f[25] * yy + f[26] * zz + f[27] * xy + f[28] * xz + f[29] * yz;
+    const T t3 = xx * (f[30] * xx + f[31] * xy + f[32] * xz + f[33] * yy + f[34] * zz + f[35] * yz) +
+                 yy * (f[36] * yy + f[37] * xy + f[38] * yz + f[39] * zz + f[40] * xz) +
+                 zz * (f[41] * zz + f[42] * xz + f[43] * yz + f[44] * xy);
+    return i3 * i2 * (f[23] + i2 * (q + i2 * t3));
+}
+
+template <typename T>
+GWN_HD inline T far3_eval(const T* f, T rx, T ry, T rz, bool o3) {
     T r2 = rx * rx + ry * ry + rz * rz;
     T i2, i3;
     if (sizeof(T) == 4) {
@@ -912,14 +926,46 @@ GWN_HD inline T far3_eval(const T* f, T rx, T ry, T rz) {
            f[12] * rz;
     T t2 = rx * (f[13] * xx + f[16] * rx * ry + f[17] * rx * rz + f[18] * yy + f[20] * zz + f[22] * ry * rz) +
            ry * (f[14] * yy + f[19] * ry * rz + f[21] * zz) + f[15] * zz * rz;
-    return i3 * (t0 + i2 * (t1 + i2 * t2));
+    T w = i3 * (t0 + i2 * (t1 + i2 * t2));
+    if (o3) w += far3_order3<T>(f, rx, ry, rz, xx, yy, zz, i2, i3);
+    return w;
 }
 
-GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz) {
-    float4 a = GWN_LDG(M), b = GWN_LDG(M + 1), c = GWN_LDG(M + 2), d = GWN_LDG(M + 3), e = GWN_LDG(M + 4), f4 = GWN_LDG(M + 5);
-    float f[24] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w,
-                   d.x, d.y, d.z, d.w, e.x, e.y, e.z, e.w, f4.x, f4.y, f4.z, f4.w};
-    return far3_eval<float>(f, rx, ry, rz);
+// FP32 moment block of a node or leaf: the first 6 float4 carry orders 0-2 (and
+// the order-3 constant), the next 6 only the order-3 terms, read after the
+// order-2 value is formed (fewer registers live at once)
+GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz, bool o3) {
+    float f[48];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+        const float4 a = GWN_LDG(M + v);
+        f[4 * v] = a.x;
+        f[4 * v + 1] = a.y;
+        f[4 * v + 2] = a.z;
+        f[4 * v + 3] = a.w;
+    }
+    const float r2 = rx * rx + ry * ry + rz * rz;
+    const float rs = rsqrtf(r2);
+    const float i2 = rs * rs, i3 = i2 * rs;
+    const float xx = rx * rx, yy = ry * ry, zz = rz * rz;
+    const float t0 = f[0] * rx + f[1] * ry + f[2] * rz + f[3];
+    const float t1 = f[4] * xx + f[5] * yy + f[6] * zz + f[7] * rx * ry + f[8] * rx * rz + f[9] * ry * rz + f[10] * rx +
+                     f[11] * ry + f[12] * rz;
+    const float t2 = rx * (f[13] * xx + f[16] * rx * ry + f[17] * rx * rz + f[18] * yy + f[20] * zz + f[22] * ry * rz) +
+                     ry * (f[14] * yy + f[19] * ry * rz + f[21] * zz) + f[15] * zz * rz;
+    float w = i3 * (t0 + i2 * (t1 + i2 * t2));
+    if (o3) {
+#pragma unroll
+        for (int v = 6; v < 12; ++v) {
+            const float4 a = GWN_LDG(M + v);
+            f[4 * v] = a.x;
+            f[4 * v + 1] = a.y;
+            f[4 * v + 2] = a.z;
+            f[4 * v + 3] = a.w;
+        }
+        w += far3_order3<float>(f, rx, ry, rz, xx, yy, zz, i2, i3);
+    }
+    return w;
 }
 
 // Algorithm 1 for one 3D query, FP32 (beta2l: the leaves' far test, <= 0 means beta2)
@@ -937,7 +983,7 @@ GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float bet
                 float4 h = GWN_LDG(t.lhdr + li);
                 float rx = h.x - qx, ry = h.y - qy, rz = h.z - qz;
                 if (rx * rx + ry * ry + rz * rz > beta2l * h.w) {
-                    w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
+                    w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz, t.order3);
                     done = true;
                 }
             }
@@ -946,7 +992,7 @@ GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float bet
             float4 h = GWN_LDG(t.hdr + node);
             float rx = h.x - qx, ry = h.y - qy, rz = h.z - qz;
             if (rx * rx + ry * ry + rz * rz > beta2 * h.w) {
-                w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz);
+                w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz, t.order3);
             } else {
                 int2 ch = GWN_LDG(t.child + node);
                 if (sp < kStack32) stack[sp++] = ch.y; else st |= GWN_QS_STACK_OVERFLOW;
@@ -979,7 +1025,7 @@ GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, doubl
                 const double* h = t.lhdr64 + (size_t)li * 4;
                 double rx = h[0] - qx, ry = h[1] - qy, rz = h[2] - qz;
                 if (rx * rx + ry * ry + rz * rz > beta2 * h[3]) {
-                    w += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
+                    w += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz, t.order3);
                     done = true;
                 }
             }
@@ -988,7 +1034,7 @@ GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, doubl
             const double* h = t.hdr64 + (size_t)node * 4;
             double rx = h[0] - qx, ry = h[1] - qy, rz = h[2] - qz;
             if (rx * rx + ry * ry + rz * rz > beta2 * h[3]) {
-                w += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz);
+                w += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz, t.order3);
             } else {
                 int2 ch = t.child[node];
                 if (sp < kStack64) stack[sp++] = ch.y; else st |= GWN_QS_UNRESOLVED;

@@ -25,6 +25,10 @@ struct gwn_model_s {
     // tree depth)
     int bin_ppc = 16;
     int stack_depth = 96;
+    // Taylor order the queries evaluate: the build's order, except that a 3D
+    // model built with order 3 may be evaluated at order 2 when the autotuner
+    // finds that faster at the tolerance (the order-2 coefficients are the same)
+    int eval_order = 2;
     // automatic FP64 repair (beta_repair < 0, more than 512 leaves): its far
     // tests at these multiples of beta (nodes) and beta_leaf (leaves); the
     // autotuner lowers them while the repaired values stay within 1e-7

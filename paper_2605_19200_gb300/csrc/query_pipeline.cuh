@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
             if (work && mine) wl.v[kWorkLeafTests] += 1;
             if (far) {
                 if (work) wl.v[kWorkFar] += 1;
-                w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz);
+                w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz, t.order3);
             }
             const unsigned need = __ballot_sync(full, mine && !far);
             if (need) {
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
             if (work && mine) wl.v[kWorkNodes] += 1;
             if (far) {
                 if (work) wl.v[kWorkFar] += 1;
-                w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz);
+                w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz, t.order3);
             }
             const unsigned near = __ballot_sync(full, mine && !far);
             if (near) {
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
                         const double* h = t.lhdr64 + (size_t)li * 4;
                         double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
                         if (beta2rl > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2rl * h[3]) {
-                            acc += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz);
+                            acc += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz, t.order3);
                         } else {
                             int slot = atomicAdd(R.npairs, 1);
                             if (slot < kRepairPairCap) R.pairs[slot] = make_int2(k, li);
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
                     double d2 = rx * rx + ry * ry + rz * rz;
                     if (beta2r > 0 && d2 > beta2r * h[3]) {
                         if (DIM == 2) acc += far2_eval<double>(t.mom64 + (size_t)node * kMom2F64, rx, ry);
-                        else acc += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz);
+                        else acc += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz, t.order3);
                     } else {
                         int2 ch = t.child[node];
                         c0 = ch.x;

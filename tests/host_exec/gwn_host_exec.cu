@@ -51,13 +51,14 @@ void init_tables() {
     }
 }
 
-DevTree host_tree(const HostModel& H, int leaf_far) {
+DevTree host_tree(const HostModel& H, int leaf_far, int order = 2) {
     DevTree t{};
     t.dim = H.dim;
     t.n_leaves = H.n_leaves;
     t.n_internal = H.n_leaves - 1;
     t.root = H.n_leaves > 1 ? 0 : ~0;
     t.leaf_far = leaf_far;
+    t.order3 = H.dim == 3 && order >= 3 ? 1 : 0;
     t.lhdr = H.lhdr.data();
     t.lmom = H.lmom.data();
     t.lhdr64 = H.lhdr64.data();
@@ -95,7 +96,7 @@ extern "C" int hx_query3(const gwn_patch3d* patches, size_t n, const gwn_build_o
     HostModel H;
     gwn_status code;
     if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
-    const DevTree t = host_tree(H, 1);
+    const DevTree t = host_tree(H, 1, o->order);
     for (int i = 0; i < nq; ++i) {
         const float qx = (float)q[3 * i], qy = (float)q[3 * i + 1], qz = (float)q[3 * i + 2];
         uint32_t s32 = 0, s64 = 0, sb = 0;
@@ -155,7 +156,7 @@ extern "C" int hx_leaf_paths3(const gwn_patch3d* patches, size_t n, const gwn_bu
     HostModel H;
     gwn_status code;
     if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
-    const DevTree t = host_tree(H, 1);
+    const DevTree t = host_tree(H, 1, o->order);
     if (t.n_leaves > max_leaves) return -2;
     for (int i = 0; i < nq; ++i)
         for (int l = 0; l < t.n_leaves; ++l) {
@@ -183,7 +184,7 @@ extern "C" int hx_leaf_paths64(const gwn_patch3d* patches, size_t n, const gwn_b
     HostModel H;
     gwn_status code;
     if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
-    const DevTree t = host_tree(H, 1);
+    const DevTree t = host_tree(H, 1, o->order);
     if (t.n_leaves > max_leaves) return -2;
     for (int i = 0; i < nq; ++i)
         for (int l = 0; l < t.n_leaves; ++l) {

@@ -388,3 +388,29 @@ def test_fp64_node_tables_match_the_full_evaluation(hx, shape):
     # the reference integrates at panel ratio 0.5, the repair's tables at 1.0 (the
     # repair's own 8-point ratio): they differ by the coarser rule's ~1e-9
     assert np.max(np.abs(fast[took] - ex[took])) <= 5e-9
+
+
+def test_order3_far_field_error_law(hx, oracle_lib):
+    """The order-3 term of the Taylor expansion (third-order moments; one term
+    beyond Eq. 3): its remainder falls one power of r / |x0 - q| faster, so on
+    the CAD shape at beta = beta_leaf = 4 the traversal's error against the
+    oracle's exact GWN is at most half the order-2 error, and below order 2 at
+    beta = 6; on the sphere it is nowhere above order 2 (the FP32 leaves and
+    the leaves' own Taylor terms at beta_leaf bound both there)."""
+    for name in ("cad", "sphere"):
+        if name == "cad":
+            patches, q = configs.cad_3d(1234, 120, 150)
+        else:
+            patches, q = configs.sphere_3d(n_queries=150)
+        w_ref, _ = oracle_lib.gwn3d(patches, q, near_thr=1e-6 * _diag3(patches))
+        ok = np.isfinite(w_ref)
+        e = {}
+        for order, beta in ((2, 4.0), (3, 4.0), (2, 6.0)):
+            _, _, b32, st = _run3(hx, patches, q, beta=beta, beta_leaf=4.0, order=order)
+            assert not np.any(st & api.QS_UNRESOLVED)
+            e[(order, beta)] = float(np.max(np.abs(b32[ok] - w_ref[ok])))
+        if name == "cad":
+            assert e[(3, 4.0)] <= 0.5 * e[(2, 4.0)] and e[(3, 4.0)] < e[(2, 6.0)], e
+        else:
+            assert e[(3, 4.0)] <= e[(2, 4.0)], e
+        assert e[(3, 4.0)] < 1e-4, e

@@ -107,7 +107,7 @@ def test_invalid_input_rejected(bad, code):
 
 def test_invalid_options_rejected():
     curves = [G.circle()]
-    for kw in ({"beta": 1.5}, {"order": 3}, {"repair_band": 0.7}, {"beta_repair": 1.0}):
+    for kw in ({"beta": 1.5}, {"order": 3}, {"repair_band": 0.7}, {"beta_repair": 1.0}):   # order 3 is 3D only
         with pytest.raises(gwn.GwnError, match="INVALID_ARG"):
             gwn.gwn_build_2d(curves, device=HOST_ONLY, **kw)
 
@@ -135,6 +135,38 @@ def test_3d_root_moments_match_plain_integrals(oracle_lib):
     np.testing.assert_allclose(got[:3], tot["m0"], atol=1e-10 * scale)
     np.testing.assert_allclose(got[3:12], tot["m1"].ravel(), atol=1e-10 * scale)
     np.testing.assert_allclose(got[12:39], tot["m2"].ravel(), atol=1e-10 * scale)
+
+
+def test_3d_root_moments_of_two_cubes_closed_form():
+    """Moments of orders 1-3 about the root centroid c for two disjoint cube
+    shells, from the divergence theorem: int y_i n_k = d_ik V,
+    int y_i y_j n_k = d_ik P_j + d_jk P_i and
+    int y_i y_j y_l n_k = d_ik J_jl + d_jk J_il + d_lk J_ij, with P = int_V y dV
+    and J = int_V y y dV over the solids (y = x - c).  The centroid differs from
+    the scene's reference point, so the binomial shift of every order is used."""
+    cubes = [((0.0, 0.0, 0.0), 1.0), ((3.0, 0.0, 0.0), 0.5)]
+    patches = G.cube_shell(*cubes[0]) + G.cube_shell(*cubes[1])
+    m = gwn.gwn_build_3d(patches, device=HOST_ONLY, order=3)
+    tr = m.tree()
+    c = tr["x0"][0]
+    np.testing.assert_allclose(c, [0.6, 0.0, 0.0], atol=1e-12)   # area-weighted: (24 * 0 + 6 * 3) / 30
+    V, P, J = 0.0, np.zeros(3), np.zeros((3, 3))
+    for a, h in cubes:
+        vol = (2 * h) ** 3
+        d = np.asarray(a) - c
+        V += vol
+        P += vol * d
+        J += vol * np.outer(d, d) + np.eye(3) * vol * h * h / 3
+    I = np.eye(3)
+    m1 = V * I
+    m2 = np.einsum("ik,j->ijk", I, P) + np.einsum("jk,i->ijk", I, P)
+    m3 = (np.einsum("ik,jl->ijlk", I, J) + np.einsum("jk,il->ijlk", I, J) + np.einsum("lk,ij->ijlk", I, J))
+    got = tr["mom"][0]
+    assert got.shape == (120,)
+    np.testing.assert_allclose(got[:3], 0.0, atol=1e-12)          # closed surfaces: int n = 0
+    np.testing.assert_allclose(got[3:12], m1.ravel(), atol=1e-11)
+    np.testing.assert_allclose(got[12:39], m2.ravel(), atol=1e-11)
+    np.testing.assert_allclose(got[39:120], m3.ravel(), atol=1e-11)
 
 
 def test_3d_leaf_moments_additive_over_subdivision(oracle_lib):
@@ -256,7 +288,8 @@ def _split_model_file(data):
     """(header bytes, [(name, count, payload bytes)]) of a model file."""
     import ctypes
     from paper_2605_19200_gb300 import api
-    off = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 16 + 16 + 48
+    # magic, 4 int32, primitive count, options, 5 int32 (tree header, binning, order), 2 repair factors, box
+    off = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 20 + 16 + 48
     head, arrays = data[:off], []
     for name, es in _ARRAY_ELEM:
         n = int(np.frombuffer(data[off:off + 8], dtype=np.uint64)[0])

@@ -347,6 +347,8 @@ def main():
     ap.add_argument("--query-scale", type=float, default=1.0, help="fraction of each model's queries (default 1)")
     ap.add_argument("--beta", type=float, default=BETA)
     ap.add_argument("--beta-leaf", type=float, default=0.0)
+    ap.add_argument("--tree-builder", type=int, default=-1, choices=[-1, 0, 1],
+                    help="0: Karras LBVH; 1: top-down sweep; -1: the library's default (1)")
     ap.add_argument("--order", type=int, default=2, choices=[2, 3],
                     help="Taylor order of the models' build (3: the autotuner picks order 2 or 3 per model)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
@@ -383,7 +385,8 @@ def main():
     log("workload generated")
     models, points, outs = [], [], []
     for patches, q in workload:
-        m = gwn.gwn_build_3d(patches, beta=args.beta, beta_leaf=args.beta_leaf, order=args.order)
+        m = gwn.gwn_build_3d(patches, beta=args.beta, beta_leaf=args.beta_leaf, order=args.order,
+                             tree_builder=args.tree_builder)
         models.append(m)
         pt = torch.from_numpy(q.astype(np.float32)).to(dev)
         points.append(pt)
@@ -615,6 +618,7 @@ def main():
                    "bin_points_per_cell_stack_depth_per_model": knobs,
                    "repair_beta_per_model": repair_betas,
                    "tolerance": 1e-4, "order": args.order, "eval_order_per_model": eval_orders,
+                   "tree": "Karras LBVH" if args.tree_builder == 0 else "top-down sweep",
                    "precision": "fp32 bulk + fp64 repair",
                    "l2": f"inputs larger than L2 ({total_q * 12 / 1e6:.0f} MB of points per step)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1),

@@ -135,6 +135,11 @@ typedef struct {
                               GPU, one thread per leaf or curve (1), or on the host threads (0); both give
                               the same model bit for bit.  -1 = on the GPU unless the build is host-only
                               (default -1) */
+    int32_t tree_builder;  /* the hierarchy over the leaves: 0 = Karras LBVH over the Morton codes of the
+                              leaf-box centres (Section 3.1); 1 = top-down sweep that splits each node
+                              where (leaves x radius^2) summed over the two children is least, over the
+                              three axes, so that far tests accept clusters earlier (fewer node visits
+                              per query); -1 = 1 (default -1).  Both give the same node layout */
 } gwn_build_opts;
 
 /* Fills *opts with the defaults listed above. */

@@ -50,7 +50,7 @@ class gwn_build_opts(ctypes.Structure):
                 ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double), ("repair_band", ctypes.c_double),
                 ("quad_nodes", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("n_threads", ctypes.c_int32), ("leaf_far", ctypes.c_int32), ("beta_leaf", ctypes.c_double),
-                ("adaptive_beta", ctypes.c_int32), ("device_build", ctypes.c_int32)]
+                ("adaptive_beta", ctypes.c_int32), ("device_build", ctypes.c_int32), ("tree_builder", ctypes.c_int32)]
 
 
 class gwn_query_opts(ctypes.Structure):

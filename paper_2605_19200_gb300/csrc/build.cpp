@@ -307,12 +307,13 @@ static void centre_block(int d, const double* box, double w, const double* wx, c
     }
 }
 
-void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm, int adaptive_beta) {
+// Karras LBVH (Section 3.1): leaves sorted by the Morton codes of their box
+// centres (stable, by index on equal codes), internal node i spanning the range
+// whose codes share the longest prefix, split where the next bit changes.
+static void karras_tree(const LeafSet& L, std::vector<int>* perm, std::vector<int2>* child) {
     const int d = L.dim;
     const int n = (int)L.wsum.size();
-    const int M = momn(d);
-    out->dim = d;
-    out->n_leaves = n;
+    const int ni = std::max(0, n - 1);
     // scene box of the leaf boxes for Morton quantisation
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < n; ++i)
@@ -339,9 +340,7 @@ void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* p
     std::vector<uint64_t> key(n);
     for (int i = 0; i < n; ++i) key[i] = code[(*perm)[i]];
 
-    const int ni = std::max(0, n - 1);
-    out->child.assign(ni, int2{0, 0});
-    std::vector<int> parent_of_leaf(n, -1), parent_of_node(ni, -1);
+    child->assign(ni, int2{0, 0});
     Karras K{key, n};
     for (int i = 0; i < ni; ++i) {
         int dir = (K.delta(i, i + 1) - K.delta(i, i - 1)) >= 0 ? 1 : -1;
@@ -361,9 +360,102 @@ void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* p
         int gamma = i + s * dir + std::min(dir, 0);
         int left = (std::min(i, j) == gamma) ? ~gamma : gamma;
         int right = (std::max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-        out->child[i] = int2{left, right};
-        if (left < 0) parent_of_leaf[~left] = i; else parent_of_node[left] = i;
-        if (right < 0) parent_of_leaf[~right] = i; else parent_of_node[right] = i;
+        (*child)[i] = int2{left, right};
+    }
+}
+
+// Top-down sweep builder.  The leaves of a node (a range of perm) are split
+// where k |D_L|^2 + (m - k) |D_R|^2 is least, D the diagonal of each side's box
+// union and k the leaves on the left, over the three axes with the leaves
+// sorted by box centre along the axis (prefix and suffix unions give every
+// split of an axis in one pass).  A node is visited when a query comes within
+// beta r of it, so small radii over many leaves cut the visits per query;
+// weighting each side by its leaf count keeps the split from peeling off
+// single leaves.  Internal nodes are numbered in preorder (root 0, left child
+// = parent + 1), leaves are ~(position in perm), as the Karras build numbers
+// them.
+static void topdown_tree(const LeafSet& L, std::vector<int>* perm, std::vector<int2>* child) {
+    const int d = L.dim;
+    const int n = (int)L.wsum.size();
+    perm->resize(n);
+    std::iota(perm->begin(), perm->end(), 0);
+    child->assign(std::max(0, n - 1), int2{0, 0});
+    if (n < 2) return;
+    auto lo = [&](int i, int k) { return L.box[(size_t)i * 2 * d + k]; };
+    auto hi = [&](int i, int k) { return L.box[(size_t)i * 2 * d + d + k]; };
+    struct Task {
+        int b, e, parent, side;
+    };
+    std::vector<Task> st{{0, n, -1, 0}};
+    std::vector<int> ord, best_ord;
+    std::vector<double> suf;  // suffix diagonal^2
+    int next = 0;
+    while (!st.empty()) {
+        const Task t = st.back();
+        st.pop_back();
+        const int id = next++;
+        if (t.parent >= 0) (t.side ? (*child)[t.parent].y : (*child)[t.parent].x) = id;
+        const int m = t.e - t.b;
+        double best = 1e300;
+        int best_k = m / 2;
+        best_ord.assign(perm->begin() + t.b, perm->begin() + t.e);
+        for (int ax = 0; ax < d; ++ax) {
+            ord.assign(perm->begin() + t.b, perm->begin() + t.e);
+            std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+                const double ca = lo(a, ax) + hi(a, ax), cb = lo(b, ax) + hi(b, ax);
+                return ca < cb || (ca == cb && a < b);
+            });
+            suf.assign(m + 1, 0.0);
+            double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
+            for (int j = m - 1; j >= 1; --j) {
+                double dd = 0;
+                for (int k = 0; k < d; ++k) {
+                    blo[k] = std::min(blo[k], lo(ord[j], k));
+                    bhi[k] = std::max(bhi[k], hi(ord[j], k));
+                    dd += (bhi[k] - blo[k]) * (bhi[k] - blo[k]);
+                }
+                suf[j] = dd;
+            }
+            double plo[3] = {1e300, 1e300, 1e300}, phi[3] = {-1e300, -1e300, -1e300};
+            bool improved = false;
+            for (int j = 0; j < m - 1; ++j) {
+                double dd = 0;
+                for (int k = 0; k < d; ++k) {
+                    plo[k] = std::min(plo[k], lo(ord[j], k));
+                    phi[k] = std::max(phi[k], hi(ord[j], k));
+                    dd += (phi[k] - plo[k]) * (phi[k] - plo[k]);
+                }
+                const double cost = (j + 1) * dd + (m - j - 1) * suf[j + 1];
+                if (cost < best) {
+                    best = cost;
+                    best_k = j + 1;
+                    improved = true;
+                }
+            }
+            if (improved) best_ord = ord;
+        }
+        std::copy(best_ord.begin(), best_ord.end(), perm->begin() + t.b);
+        const int mid = t.b + best_k;
+        // right first, so that the left subtree takes the next preorder numbers
+        if (t.e - mid == 1) (*child)[id].y = ~mid;
+        else st.push_back({mid, t.e, id, 1});
+        if (mid - t.b == 1) (*child)[id].x = ~t.b;
+        else st.push_back({t.b, mid, id, 0});
+    }
+}
+
+void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm, int adaptive_beta,
+                int tree_builder) {
+    const int d = L.dim;
+    const int n = (int)L.wsum.size();
+    const int M = momn(d);
+    out->dim = d;
+    out->n_leaves = n;
+    const int ni = std::max(0, n - 1);
+    if (tree_builder != 0) {
+        topdown_tree(L, perm, &out->child);
+    } else {
+        karras_tree(L, perm, &out->child);
     }
 
     // up-sweep in post-order (children before parents)
@@ -657,7 +749,7 @@ std::string build_model_2d(const gwn_curve2d* curves, size_t n, const gwn_build_
         S.wx[i * 2 + 1] = len * (0.5 * (a[1] + b[1]) + S.xref[1]);
     }
     std::vector<int> perm;
-    build_tree(S, o.order, out, &perm, o.adaptive_beta);
+    build_tree(S, o.order, out, &perm, o.adaptive_beta, o.tree_builder);
     out->lo[0] = slo[0]; out->lo[1] = slo[1];
     out->hi[0] = shi[0]; out->hi[1] = shi[1];
     out->leaf_prim.resize(nl);

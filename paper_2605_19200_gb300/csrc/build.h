@@ -68,11 +68,13 @@ std::string build_model_2d(const gwn_curve2d* curves, size_t n, const gwn_build_
 std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build_opts& o, HostModel* out,
                            gwn_status* code);
 
-// Generic LBVH + up-sweep + centring + packing of the node arrays.  perm
-// receives the BVH leaf order (perm[i] = input leaf index of BVH leaf i).
-// adaptive_beta: scale each cluster's far-test radius by its fill (see
-// gwn_build_opts::adaptive_beta).
-void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm, int adaptive_beta = 0);
+// Hierarchy (tree_builder 0: Karras LBVH; else the top-down sweep, see
+// gwn_build_opts::tree_builder) + up-sweep + centring + packing of the node
+// arrays.  perm receives the BVH leaf order (perm[i] = input leaf index of BVH
+// leaf i).  adaptive_beta: scale each cluster's far-test radius by its fill
+// (see gwn_build_opts::adaptive_beta).
+void build_tree(const LeafSet& L, int order, HostModel* out, std::vector<int>* perm, int adaptive_beta = 0,
+                int tree_builder = 1);
 
 // Validation of a clamped NURBS knot vector; returns "" when valid.
 std::string check_knots(int degree, int n_ctrl, const double* knots);

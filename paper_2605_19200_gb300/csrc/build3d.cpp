@@ -684,7 +684,7 @@ std::string build_model_3d(const gwn_patch3d* patches, size_t n, const gwn_build
         S.wsum[i] = L.area;
     }
     std::vector<int> perm;
-    build_tree(S, o.order, out, &perm, o.adaptive_beta);
+    build_tree(S, o.order, out, &perm, o.adaptive_beta, o.tree_builder);
     for (int k = 0; k < 3; ++k) { out->lo[k] = slo[k]; out->hi[k] = shi[k]; }
 
     // pack leaves in BVH order

@@ -230,6 +230,7 @@ gwn_status check_opts(const gwn_build_opts& o, int dim) {
         return fail(GWN_ERR_INVALID_ARG, dim == 3 ? "order must be 0, 1, 2 or 3" : "order must be 0, 1 or 2");
     if (o.adaptive_beta != 0 && o.adaptive_beta != 1) return fail(GWN_ERR_INVALID_ARG, "adaptive_beta must be 0 or 1");
     if (o.device_build < -1 || o.device_build > 1) return fail(GWN_ERR_INVALID_ARG, "device_build must be -1, 0 or 1");
+    if (o.tree_builder < -1 || o.tree_builder > 1) return fail(GWN_ERR_INVALID_ARG, "tree_builder must be -1, 0 or 1");
     if (!(o.beta_repair <= 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be <= 0 or >= 2");
     if (!(o.repair_band >= 0.0 && o.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
     if (o.quad_nodes < 1 || o.quad_nodes > 32) return fail(GWN_ERR_INVALID_ARG, "quad_nodes must be 1..32");
@@ -703,6 +704,7 @@ void gwn_default_build_opts(gwn_build_opts* o) {
     o->beta_leaf = 0.0;
     o->adaptive_beta = 0;
     o->device_build = -1;
+    o->tree_builder = -1;
 }
 
 void gwn_default_query_opts(gwn_query_opts* q) {

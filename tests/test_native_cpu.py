@@ -38,9 +38,13 @@ def _leaves_under(child, node):
     return out
 
 
-def test_tree_is_a_valid_binary_radix_tree():
+@pytest.mark.parametrize("tree_builder", [0, 1])
+def test_tree_is_a_valid_binary_tree(tree_builder):
+    """Both builders: every leaf under the root exactly once, every internal node
+    but the root the child of exactly one node; the top-down sweep numbers its
+    nodes in preorder (an internal left child is its parent + 1)."""
     curves, _ = configs.loops_2d(n_loops=20, per_loop=30, res=8)
-    m = gwn.gwn_build_2d(curves, device=HOST_ONLY)
+    m = gwn.gwn_build_2d(curves, device=HOST_ONLY, tree_builder=tree_builder)
     info = m.info()
     tr = m.tree()
     n = info["n_leaves"]
@@ -49,6 +53,41 @@ def test_tree_is_a_valid_binary_radix_tree():
     assert sorted(leaves) == list(range(n))
     internal = [c for pair in tr["child"] for c in pair if c >= 0]
     assert sorted(internal) == list(range(1, n - 1))
+    if tree_builder == 1:
+        left = tr["child"][:, 0]
+        k = np.nonzero(left >= 0)[0]
+        np.testing.assert_array_equal(left[k], k + 1)
+        # leaves in depth-first order: each subtree covers a contiguous range of them
+        for node in range(0, n - 1, 97):
+            L = sorted(_leaves_under(tr["child"], node))
+            assert L == list(range(L[0], L[0] + len(L)))
+
+
+def _sum_r3_and_visits(m, q, beta):
+    """Sum of cubed node radii and the internal-node visits per query of
+    Algorithm 1's traversal (far test |q - x0| > beta r), counted on the host."""
+    tr = m.tree()
+    child, x0, r = tr["child"], tr["x0"], tr["r"]
+    visits, front = 0, [(0, np.arange(len(q)))]
+    while front:
+        node, idx = front.pop()
+        visits += len(idx)
+        near = idx[np.sum((q[idx] - x0[node]) ** 2, 1) <= (beta * r[node]) ** 2]
+        if len(near):
+            front.extend((c, near) for c in child[node] if c >= 0)
+    return float(np.sum(r ** 3)), visits / len(q)
+
+
+def test_topdown_tree_has_smaller_radii_than_the_lbvh():
+    """On a CAD solid the top-down sweep's nodes are tighter than the Karras
+    LBVH's: smaller summed r^3 and fewer internal-node visits per uniform query
+    at beta = 5 (the same leaves, the same radius definition)."""
+    patches, q = configs.cad_3d(4321, 1400, 4000)
+    res = {}
+    for tb in (0, 1):
+        m = gwn.gwn_build_3d(patches, device=HOST_ONLY, tree_builder=tb, beta=5.0, beta_leaf=3.5)
+        res[tb] = _sum_r3_and_visits(m, q, 5.0)
+    assert res[1][0] < 0.95 * res[0][0] and res[1][1] < 0.95 * res[0][1], res
 
 
 def test_subdivision_respects_the_box_threshold(oracle_lib):

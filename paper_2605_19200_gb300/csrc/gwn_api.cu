@@ -599,15 +599,12 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
                 const int* list = round == 0 ? perm : (round == 1 ? ws.olist : ws.olist2);
                 int* olist_out = round == 1 ? ws.olist2 : ws.olist;
                 const int* ndev = round == 0 ? nullptr : ws.counters + 5;
-                if (m->stack_depth <= 64)
-                    k_trav3<64><<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
-                                                  ndev, olist_out);
-                else if (m->stack_depth <= 96)
-                    k_trav3<96><<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
-                                                  ndev, olist_out);
-                else
-                    k_trav3<128><<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work,
-                                                   ndev, olist_out);
+                // instance by warp-stack size and by whether the order-3 terms are evaluated
+                auto trav = m->stack_depth <= 64
+                                ? (m->tree.order3 ? k_trav3<64, true> : k_trav3<64, false>)
+                                : m->stack_depth <= 96 ? (m->tree.order3 ? k_trav3<96, true> : k_trav3<96, false>)
+                                                       : (m->tree.order3 ? k_trav3<128, true> : k_trav3<128, false>);
+                trav<<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work, ndev, olist_out);
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
                 GWN_CUDA_TRY(cudaGetLastError());
                 // 3. exact leaves, sorted by leaf (one atomic per run of a leaf); far

@@ -146,27 +146,33 @@ __device__ __forceinline__ void flush_warp_pairs(const int2* buf, const unsigned
 
 // traversal with deferred 3D leaves, one packet per warp: the 32 queries of a
 // warp (neighbours in the binned order) walk the tree together.  The warp
-// holds one node and the mask of its lanes that still need that subtree; each
-// lane applies the far test, far lanes add the node's Taylor term, and the
-// children are visited (the second one through a warp stack in shared memory)
-// with the mask of the lanes for which the node was near.  Node and moment
-// loads are then the same address for the whole warp, and lanes never wait on
-// each other's different branches.  Binned queries share most of their paths
-// (the union of a warp's visits is ~1.05x the longest single path), so the
-// packet costs little extra work.  Exact 3D leaves go to the pair list: at a
-// leaf, the lanes that need it exactly write their (point, leaf) pairs next to
-// each other into the warp's shared-memory buffer, which is flushed to the list
-// with one atomic when full, so the list comes out in runs of one leaf (the
-// pair kernels read a leaf's data once per run, with no sort by leaf).  Every
-// thread of the grid reaches the flushes (lanes past the end of the list take
-// part with an empty mask).
+// holds one internal node and the mask of its lanes for which that node was
+// near; an iteration tests both children of the node for those lanes: far
+// lanes add the child's Taylor term, and for a leaf the lanes that need it
+// exactly write their pairs, for an internal child the lanes for which it is
+// near need its subtree.  The walk goes on into a near child and keeps the
+// other (if it is near too) on a warp stack in shared memory.  Node and moment
+// loads are the same address for the whole warp, and lanes never wait on each
+// other's different branches.  Binned queries share most of their paths (the
+// union of a warp's visits is ~1.05x the longest single path), so the packet
+// costs little extra work; testing the children inline makes one loop
+// iteration and at most one stack entry per near node, not one per node
+// tested.  Exact 3D leaves go to the pair list: at a leaf, the lanes that need
+// it exactly write their (point, leaf) pairs next to each other into the
+// warp's shared-memory buffer, which is flushed to the list with one atomic
+// when full, so the list comes out in runs of one leaf (the pair kernels read a
+// leaf's data once per run, with no sort by leaf).  Every thread of the grid
+// reaches the flushes (lanes past the end of the list take part with an empty
+// mask).
 // n_dev != nullptr: the point list `perm` holds *n_dev entries (a later round
 // over the points whose pairs overflowed; their indices go to `olist_out`)
-// STACK: entries of the warp stack (pending second children along the packet's
-// path), chosen per model from its tree depth (64, 96 or 128)
+// STACK: entries of the warp stack (pending near siblings along the packet's
+// path), chosen per model from its tree depth (64, 96 or 128).  O3: the model
+// evaluates the order-3 terms (a separate instance, so that order-2 models do
+// not pay its registers)
 constexpr int kPacketStack = 96;  // entries per warp of the 2D traversal
 
-template <int STACK>
+template <int STACK, bool O3>
 __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int dtype, int n, const int* perm,
                                                float beta2, float beta2l, Workspace ws, unsigned long long* work,
                                                const int* n_dev, int* olist_out) {
@@ -191,20 +197,21 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
     int bcnt = 0;                      // warp-uniform: entries in buf
     unsigned ovf = 0;                  // lanes with pairs that did not fit the list
     int sp = 0;                        // warp-uniform
-    int node = t.root;                 // warp-uniform
-    unsigned mask = __ballot_sync(full, active);
-    while (mask) {
-        const bool mine = (mask >> lane) & 1u;
-        bool descend = false;
-        if (node < 0) {
-            const int li = ~node;
+
+    // Test node or leaf c for the lanes of `msk` (warp-uniform c and msk):
+    // Taylor terms for the far lanes, pairs for the lanes that need a leaf
+    // exactly; returns the lanes for which an internal c is near.
+    auto test = [&](int c, unsigned msk) -> unsigned {
+        const bool mine = (msk >> lane) & 1u;
+        if (c < 0) {
+            const int li = ~c;
             const float4 h = GWN_LDG(t.lhdr + li);
             const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
             const bool far = mine && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2l * h.w;
             if (work && mine) wl.v[kWorkLeafTests] += 1;
             if (far) {
                 if (work) wl.v[kWorkFar] += 1;
-                w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz, t.order3);
+                w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz, O3);
             }
             const unsigned need = __ballot_sync(full, mine && !far);
             if (need) {
@@ -222,31 +229,42 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
                 }
                 bcnt += nn;
             }
-        } else {
-            const float4 h = GWN_LDG(t.hdr + node);
-            const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
-            const bool far = mine && rx * rx + ry * ry + rz * rz > beta2 * h.w;
-            if (work && mine) wl.v[kWorkNodes] += 1;
-            if (far) {
-                if (work) wl.v[kWorkFar] += 1;
-                w += far3_node32(t.mom + (size_t)node * kMom3Vec, rx, ry, rz, t.order3);
-            }
-            const unsigned near = __ballot_sync(full, mine && !far);
-            if (near) {
-                const int2 ch = GWN_LDG(t.child + node);
+            return 0u;
+        }
+        const float4 h = GWN_LDG(t.hdr + c);
+        const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
+        const bool far = mine && rx * rx + ry * ry + rz * rz > beta2 * h.w;
+        if (work && mine) wl.v[kWorkNodes] += 1;
+        if (far) {
+            if (work) wl.v[kWorkFar] += 1;
+            w += far3_node32(t.mom + (size_t)c * kMom3Vec, rx, ry, rz, O3);
+        }
+        return __ballot_sync(full, mine && !far);
+    };
+
+    int node = t.root;  // warp-uniform
+    unsigned mask = __ballot_sync(full, active);
+    if (mask) mask = test(node, mask);  // the root itself (a leaf when the model has one)
+    while (mask) {
+        const int2 ch = GWN_LDG(t.child + node);
+        const unsigned na = test(ch.x, mask);
+        const unsigned nb = test(ch.y, mask);
+        if (na) {
+            if (nb) {
                 if (sp < STACK) {
-                    if (lane == 0) stk[sp] = make_int2(ch.y, (int)near);
+                    if (lane == 0) stk[sp] = make_int2(ch.y, (int)nb);
                     ++sp;
-                } else if ((near >> lane) & 1u) {
+                } else if ((nb >> lane) & 1u) {
                     st |= GWN_QS_STACK_OVERFLOW;  // the second subtree is dropped for these lanes
                 }
                 __syncwarp();
-                node = ch.x;
-                mask = near;
-                descend = true;
             }
-        }
-        if (!descend) {
+            node = ch.x;
+            mask = na;
+        } else if (nb) {
+            node = ch.y;
+            mask = nb;
+        } else {
             if (sp == 0) break;
             --sp;
             const int2 e = stk[sp];

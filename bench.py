@@ -131,8 +131,11 @@ def aggregate_ranks(ms, units_per_rank, world, device):
 def flops_traversal(w, order3=False):
     # per internal node / leaf visited: far test (10); per Taylor evaluation: 72
     # at order 2, 120 with the order-3 terms (the quadratic and quartic of the
-    # third-order moments)
-    return 10 * (w["nodes"] + w["leaf_tests"]) + (120 if order3 else 72) * w["far"]
+    # third-order moments); per query and cluster taken by its packet's local
+    # expansion: 7 (one lane forms the cluster's ~200-flop expansion for the 32
+    # queries of the warp, and the warp sums 10 coefficients)
+    return (10 * (w["nodes"] + w["leaf_tests"]) + (120 if order3 else 72) * w["far"] +
+            7 * w.get("local_nodes", 0))
 
 
 FAST_NODE_FLOPS = 34    # a node read from a curve's node table: r, |r|, s.r, s x r, the integrand (+ 2 SFU ops)
@@ -347,6 +350,8 @@ def main():
     ap.add_argument("--query-scale", type=float, default=1.0, help="fraction of each model's queries (default 1)")
     ap.add_argument("--beta", type=float, default=BETA)
     ap.add_argument("--beta-leaf", type=float, default=0.0)
+    ap.add_argument("--local-ratio", type=float, default=0.0,
+                    help="packet local expansion ratio of the models (<= 0: off, the default)")
     ap.add_argument("--tree-builder", type=int, default=-1, choices=[-1, 0, 1],
                     help="0: Karras LBVH; 1: top-down sweep; -1: the library's default (1)")
     ap.add_argument("--order", type=int, default=2, choices=[2, 3],
@@ -386,7 +391,7 @@ def main():
     models, points, outs = [], [], []
     for patches, q in workload:
         m = gwn.gwn_build_3d(patches, beta=args.beta, beta_leaf=args.beta_leaf, order=args.order,
-                             tree_builder=args.tree_builder)
+                             tree_builder=args.tree_builder, local_ratio=args.local_ratio)
         models.append(m)
         pt = torch.from_numpy(q.astype(np.float32)).to(dev)
         points.append(pt)
@@ -401,6 +406,7 @@ def main():
     knobs = [(m.info()["bin_points_per_cell"], m.info()["stack_depth"]) for m in models]
     repair_betas = [(round(m.info()["beta_repair"], 2), round(m.info()["beta_repair_leaf"], 2)) for m in models]
     eval_orders = [m.info()["eval_order"] for m in models]
+    local_ratios = [m.info()["local_ratio"] for m in models]
     n_leaves = sum(m.info()["n_leaves"] for m in models)
     n_patches = sum(len(p) for p, _ in workload)
     stream = torch.cuda.current_stream(dev)
@@ -454,7 +460,7 @@ def main():
     us = {"k_trav3": 0.0, "k_pair_fast": 0.0, "k_pair_eval": 0.0}
     fl = {"k_trav3": 0.0, "k_pair_fast": 0.0, "k_pair_eval": 0.0}
     repaired, pairs, near, full_pairs = 0, 0, 0, 0
-    work_tot = {"fast_nodes": 0, "gl_nodes": 0, "hits": 0, "nodes": 0, "far": 0}
+    work_tot = {"fast_nodes": 0, "gl_nodes": 0, "hits": 0, "nodes": 0, "far": 0, "local_nodes": 0}
     for m, p, o in zip(models, points, outs):
         m.query(p, out=o, stream=stream, profile=True)
         s = m.last_query_stats()
@@ -470,7 +476,7 @@ def main():
         pairs += w["pairs"]
         near += w["near_band"]
         full_pairs += w["full_pairs"]
-        for k in ("fast_nodes", "gl_nodes", "hits", "nodes", "far"):
+        for k in ("fast_nodes", "gl_nodes", "hits", "nodes", "far", "local_nodes"):
             work_tot[k] += w[k]
     log("profiled and counted")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -603,10 +609,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_serve:
         serving = serving_leg(gwn, args.serve_seconds, log)
 
-    # kernels per chunk of up to 2^19 points: bin, scan, scatter; 3 rounds of traversal, pair histogram,
+    # kernels per chunk of up to 2^19 points: box, bin, scan, scatter; 3 rounds of traversal, pair histogram,
     # scan, pair sort, node-table pairs, full pairs (+ round switch x2); near band, overflow, finish, the
     # chunk's own repair x4 (normally empty), counter accumulate; per query: repair x4 + its accumulate
-    launches_per_step = sum(31 * math.ceil(p.shape[0] / (1 << 19)) + 5 for p in points)
+    launches_per_step = sum(32 * math.ceil(p.shape[0] / (1 << 19)) + 5 for p in points)
     line = {
         "metric": "GWN queries/s (batched containment, 16 trimmed-NURBS models)",
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
@@ -619,6 +625,7 @@ def main():
                    "repair_beta_per_model": repair_betas,
                    "tolerance": 1e-4, "order": args.order, "eval_order_per_model": eval_orders,
                    "tree": "Karras LBVH" if args.tree_builder == 0 else "top-down sweep",
+                   "local_ratio_per_model": local_ratios,
                    "precision": "fp32 bulk + fp64 repair",
                    "l2": f"inputs larger than L2 ({total_q * 12 / 1e6:.0f} MB of points per step)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 1),
@@ -639,7 +646,8 @@ def main():
                  "bernstein_nodes_per_query": work_tot["gl_nodes"] / total_q,
                  "foot_point_searches_per_query": work_tot["hits"] / total_q,
                  "nodes_visited_per_query": work_tot["nodes"] / total_q,
-                 "taylor_terms_per_query": work_tot["far"] / total_q},
+                 "taylor_terms_per_query": work_tot["far"] / total_q,
+                 "packet_local_terms_per_query": work_tot["local_nodes"] / total_q},
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
     }

@@ -140,6 +140,8 @@ typedef struct {
                               where (leaves x radius^2) summed over the two children is least, over the
                               three axes, so that far tests accept clusters earlier (fewer node visits
                               per query); -1 = 1 (default -1).  Both give the same node layout */
+    double local_ratio;    /* 3D: the model's packet local-expansion ratio (gwn_query_opts.local_ratio),
+                              >= 4; <= 0 = off (default 0) */
 } gwn_build_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -154,6 +156,18 @@ typedef struct {
     double beta_leaf;   /* 0 = the model's */
     double repair_band; /* > 0: re-evaluate in FP64 when |w - round(w) +- 1/2| < this band instead of the
                            model's (GWN_PREC_FP32_REPAIR only); 0 = the model's (default 0) */
+    double local_ratio; /* 3D, order-2 evaluation: a cluster that every query of a warp's packet (32 binned
+                           queries) reaches, that is far for the packet's whole box and lies beyond this
+                           many packet radii is taken by a second-order local expansion about the
+                           packet's centre -- one expansion per cluster for the warp instead of one Taylor
+                           term per query (a local-expansion far field; the paper evaluates every term per
+                           query).  Its remainder falls like (1/ratio)^3 of the cluster's term, and the
+                           remainders of the clusters a packet takes add up: with ~700 clusters per
+                           packet, ratio 16 moved values by up to 7.6e-5 and 32 keeps them within 2e-5.  It pays
+                           only where a packet's 32 queries are close together next to the clusters the
+                           traversal accepts: on queries uniform in a CAD model's box at 1.2M points it
+                           took 3 of 787 terms per query and slowed the traversal.  0 = the model's;
+                           < 0 = off; >= 4 = this ratio (default 0) */
 } gwn_query_opts;
 
 void gwn_default_query_opts(gwn_query_opts* opts);
@@ -237,6 +251,8 @@ typedef struct {
     double beta_repair_leaf; /* far-test factor of the FP64 repair's leaves (0: exact sum over every leaf) */
     int32_t eval_order;     /* Taylor order the queries evaluate: `order`, or 2 for a 3D model built with
                                order 3 whose autotuner found order 2 faster at the tolerance */
+    double local_ratio;     /* 3D: the model's packet local-expansion ratio (gwn_query_opts.local_ratio);
+                               0 = off */
 } gwn_model_stats;
 
 gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
@@ -257,7 +273,8 @@ gwn_status gwn_model_info(gwn_model model, gwn_model_stats* stats);
  *   out[15] with count_work: Gauss-Legendre nodes read from the node tables
  *   out[16..17] with profile: the exact-leaf time split into the node-table
  *     kernel and the full evaluator (microseconds)
- *   out[18..19] zero (reserved) */
+ *   out[18] with count_work: clusters taken by packets' local expansions
+ *   out[19] zero (reserved) */
 gwn_status gwn_last_query_stats(gwn_model model, int64_t* out);
 
 /* Copy per-leaf records to host memory for inspection (used by the tests).

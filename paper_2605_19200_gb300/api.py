@@ -50,13 +50,14 @@ class gwn_build_opts(ctypes.Structure):
                 ("beta", ctypes.c_double), ("beta_repair", ctypes.c_double), ("repair_band", ctypes.c_double),
                 ("quad_nodes", ctypes.c_int32), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("n_threads", ctypes.c_int32), ("leaf_far", ctypes.c_int32), ("beta_leaf", ctypes.c_double),
-                ("adaptive_beta", ctypes.c_int32), ("device_build", ctypes.c_int32), ("tree_builder", ctypes.c_int32)]
+                ("adaptive_beta", ctypes.c_int32), ("device_build", ctypes.c_int32), ("tree_builder", ctypes.c_int32),
+                ("local_ratio", ctypes.c_double)]
 
 
 class gwn_query_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double),
                 ("count_work", ctypes.c_int32), ("profile", ctypes.c_int32), ("beta_leaf", ctypes.c_double),
-                ("repair_band", ctypes.c_double)]
+                ("repair_band", ctypes.c_double), ("local_ratio", ctypes.c_double)]
 
 
 class gwn_model_stats(ctypes.Structure):
@@ -66,7 +67,8 @@ class gwn_model_stats(ctypes.Structure):
                 ("repair_band", ctypes.c_double), ("order", ctypes.c_int32), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("beta_leaf", ctypes.c_double), ("device", ctypes.c_int32),
                 ("bin_points_per_cell", ctypes.c_int32), ("stack_depth", ctypes.c_int32),
-                ("beta_repair_leaf", ctypes.c_double), ("eval_order", ctypes.c_int32)]
+                ("beta_repair_leaf", ctypes.c_double), ("eval_order", ctypes.c_int32),
+                ("local_ratio", ctypes.c_double)]
 
 
 class gwn_serve_opts(ctypes.Structure):
@@ -223,7 +225,7 @@ class Model:
         _check(lib().gwn_last_query_stats(self.handle, out.ctypes.data))
         names = ["pairs", "repaired", "near_band", "overflow", "nodes", "leaf_tests", "far", "leaves",
                  "gl_nodes", "gl_deg", "hits", "chords", "trav_us", "leaf_us", "full_pairs", "fast_nodes",
-                 "fast_us", "full_us"]
+                 "fast_us", "full_us", "local_nodes"]
         return {k: int(out[i]) for i, k in enumerate(names)}
 
     def leaves(self):
@@ -246,10 +248,10 @@ class Model:
 
     def query(self, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
               want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
-              out=None, beta_leaf: float = 0.0, repair_band: float = 0.0):
+              out=None, beta_leaf: float = 0.0, repair_band: float = 0.0, local_ratio: float = 0.0):
         return gwn_query(self, points, mode=mode, precision=precision, beta=beta, stream=stream,
                          want_label=want_label, want_status=want_status, count_work=count_work, profile=profile,
-                         out=out, beta_leaf=beta_leaf, repair_band=repair_band)
+                         out=out, beta_leaf=beta_leaf, repair_band=repair_band, local_ratio=local_ratio)
 
 
 def marshal_curves(curves: Sequence):
@@ -352,13 +354,14 @@ def _check_device(model: Model, pts, out):
 
 def gwn_query(model: Model, points, mode: int = MODE_BVH, precision: int = -1, beta: float = 0.0, stream=None,
               want_label: bool = True, want_status: bool = True, count_work: bool = False, profile: bool = False,
-              out=None, beta_leaf: float = 0.0, repair_band: float = 0.0):
+              out=None, beta_leaf: float = 0.0, repair_band: float = 0.0, local_ratio: float = 0.0):
     """GWN at points.  torch CUDA tensor -> asynchronous device call with device
     outputs; numpy array or CPU tensor -> host call (staged, synchronous).
     Returns (w float64, label int32 or None, status uint32/int32 or None).
     `out` may supply preallocated outputs (w, label or None, status or None)."""
     q = default_query_opts(mode=mode, precision=precision, beta=beta, count_work=int(count_work),
-                           profile=int(profile), beta_leaf=beta_leaf, repair_band=repair_band)
+                           profile=int(profile), beta_leaf=beta_leaf, repair_band=repair_band,
+                           local_ratio=local_ratio)
     try:
         import torch
     except Exception:  # pragma: no cover

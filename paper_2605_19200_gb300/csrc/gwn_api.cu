@@ -231,6 +231,8 @@ gwn_status check_opts(const gwn_build_opts& o, int dim) {
     if (o.adaptive_beta != 0 && o.adaptive_beta != 1) return fail(GWN_ERR_INVALID_ARG, "adaptive_beta must be 0 or 1");
     if (o.device_build < -1 || o.device_build > 1) return fail(GWN_ERR_INVALID_ARG, "device_build must be -1, 0 or 1");
     if (o.tree_builder < -1 || o.tree_builder > 1) return fail(GWN_ERR_INVALID_ARG, "tree_builder must be -1, 0 or 1");
+    if (!(o.local_ratio <= 0.0 || (o.local_ratio >= 4.0 && o.local_ratio < 1e6)))
+        return fail(GWN_ERR_INVALID_ARG, "local_ratio must be <= 0 or in [4, 1e6)");
     if (!(o.beta_repair <= 0.0 || o.beta_repair >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_repair must be <= 0 or >= 2");
     if (!(o.repair_band >= 0.0 && o.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
     if (o.quad_nodes < 1 || o.quad_nodes > 32) return fail(GWN_ERR_INVALID_ARG, "quad_nodes must be 1..32");
@@ -405,6 +407,7 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     w.rlist_g = (int*)carve(n * sizeof(int));
     w.rst = (uint32_t*)carve(n * sizeof(uint32_t));
     w.gcount = (int*)carve(8 * sizeof(int));
+    w.bbox = (unsigned*)carve(8 * sizeof(unsigned));
     w.rcap = (int)n;
     w.olist = (int*)carve((dim != 2 ? n : 0) * sizeof(int));
     w.olist2 = (int*)carve((dim != 2 ? n : 0) * sizeof(int));
@@ -476,6 +479,9 @@ static QueryParams query_params(const gwn_model_s* m, const gwn_query_opts& qo, 
     const double brl = br > 0 ? (automatic ? m->repair_leaf_factor * beta_leaf : br * beta_leaf / beta) : 0.0;
     p.beta2_repair_leaf = brl > 0 ? brl * brl : 0.0;
     p.band = (float)(qo.repair_band > 0 ? qo.repair_band : m->opts.repair_band);
+    // packet local expansion (3D, order-2 evaluation): the query's ratio, else the model's; < 0 off
+    const double kap = qo.local_ratio != 0.0 ? qo.local_ratio : m->local_ratio;
+    p.kappa2 = m->dim == 3 && !m->tree.order3 && kap > 0 ? (float)(kap * kap) : 0.f;
     p.mode = qo.mode;
     p.precision = qo.precision >= 0 ? qo.precision : m->opts.precision;
     return p;
@@ -567,16 +573,16 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
         if (n >= 2048) {
             const int bits = m->dim == 2 ? kBinBits2 : bin_bits3(n, m->bin_ppc);
             const int cells = 1 << (m->dim * bits);
-            float3 lo = make_float3((float)m->host.lo[0], (float)m->host.lo[1], (float)m->host.lo[2]);
-            float ex[3];
-            for (int k = 0; k < 3; ++k) {
-                double e = m->host.hi[k] - m->host.lo[k];
-                ex[k] = e > 0 ? (float)(1.0 / e) : 0.f;
-            }
-            float3 inv = make_float3(ex[0], ex[1], ex[2]);
             GWN_CUDA_TRY(cudaMemsetAsync(ws.hist, 0, (size_t)cells * sizeof(int), st));
-            if (m->dim == 2) k_bin<2><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, bits, ws.key, ws.hist);
-            else k_bin<3><<<nb, B, 0, st>>>(pts, dtype, ni, lo, inv, bits, ws.key, ws.hist);
+            GWN_CUDA_TRY(cudaMemsetAsync(ws.bbox, 0, 8 * sizeof(unsigned), st));
+            const unsigned bb = (unsigned)std::min<long long>(nb, (long long)sms * 4);
+            if (m->dim == 2) {
+                k_bbox<2><<<bb, B, 0, st>>>(pts, dtype, ni, ws.bbox);
+                k_bin<2><<<nb, B, 0, st>>>(pts, dtype, ni, ws.bbox, bits, ws.key, ws.hist);
+            } else {
+                k_bbox<3><<<bb, B, 0, st>>>(pts, dtype, ni, ws.bbox);
+                k_bin<3><<<nb, B, 0, st>>>(pts, dtype, ni, ws.bbox, bits, ws.key, ws.hist);
+            }
             k_scan<<<1, 1024, 0, st>>>(ws.hist, cells);
             k_scatter_perm<<<nb, B, 0, st>>>(ni, ws.key, ws.hist, ws.perm);
             GWN_CUDA_TRY(cudaGetLastError());
@@ -599,12 +605,21 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
                 const int* list = round == 0 ? perm : (round == 1 ? ws.olist : ws.olist2);
                 int* olist_out = round == 1 ? ws.olist2 : ws.olist;
                 const int* ndev = round == 0 ? nullptr : ws.counters + 5;
-                // instance by warp-stack size and by whether the order-3 terms are evaluated
-                auto trav = m->stack_depth <= 64
-                                ? (m->tree.order3 ? k_trav3<64, true> : k_trav3<64, false>)
-                                : m->stack_depth <= 96 ? (m->tree.order3 ? k_trav3<96, true> : k_trav3<96, false>)
-                                                       : (m->tree.order3 ? k_trav3<128, true> : k_trav3<128, false>);
-                trav<<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work, ndev, olist_out);
+                // instance by warp-stack size, by whether the order-3 terms are evaluated,
+                // and by whether packets take far nodes by local expansion (order 2 only)
+                if (!m->tree.order3 && p.kappa2 > 0.f) {
+                    auto trav = m->stack_depth <= 64 ? k_trav3_local<64>
+                                                     : m->stack_depth <= 96 ? k_trav3_local<96> : k_trav3_local<128>;
+                    trav<<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work, ndev,
+                                           olist_out, p.kappa2);
+                } else {
+                    const bool o3 = m->tree.order3 != 0;
+                    auto trav = m->stack_depth <= 64   ? (o3 ? k_trav3<64, true> : k_trav3<64, false>)
+                                : m->stack_depth <= 96 ? (o3 ? k_trav3<96, true> : k_trav3<96, false>)
+                                                       : (o3 ? k_trav3<128, true> : k_trav3<128, false>);
+                    trav<<<nb, B, 0, st>>>(m->tree, pts, dtype, ni, list, p.beta2, p.beta2_leaf, ws, p.work, ndev,
+                                           olist_out);
+                }
                 if (prof && round == 0) GWN_CUDA_TRY(cudaEventRecord(ev[1], st));
                 GWN_CUDA_TRY(cudaGetLastError());
                 // 3. exact leaves, sorted by leaf (one atomic per run of a leaf); far
@@ -702,6 +717,7 @@ void gwn_default_build_opts(gwn_build_opts* o) {
     o->adaptive_beta = 0;
     o->device_build = -1;
     o->tree_builder = -1;
+    o->local_ratio = 0.0;
 }
 
 void gwn_default_query_opts(gwn_query_opts* q) {
@@ -713,6 +729,7 @@ void gwn_default_query_opts(gwn_query_opts* q) {
     q->profile = 0;
     q->beta_leaf = 0.0;
     q->repair_band = 0.0;
+    q->local_ratio = 0.0;
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -886,7 +903,9 @@ static gwn_status autotune(gwn_model_s* m) {
     // Counted flops do not weigh the kernels alike (the traversal's far tests and
     // Taylor terms issue about twice the instructions per counted flop of the
     // node-table leaves), so among the accurate candidates the cheapest four by
-    // count of each order are timed on a uniform sample of the model's box, and
+    // count of each order are timed on 2^19 points uniform in the model's box (a
+    // full chunk of a large query: smaller samples bin and pair differently and
+    // flipped the choice between close candidates from run to run), and
     // the fastest is kept; then the binning's target points per cell is timed
     // the same way (the sample is binned at the resolution its size gives, as a
     // query is).
@@ -899,7 +918,7 @@ static gwn_status autotune(gwn_model_s* m) {
                 if (per_order[std::get<3>(c)]++ < 4) keep.push_back(c);
             ok_cands.swap(keep);
         }
-        const int nt = 1 << 16;
+        const int nt = 1 << 19;  // one full chunk: binned and paired as a large query is
         std::vector<float> tp((size_t)nt * d);
         for (int i = 0; i < nt; ++i)
             for (int k = 0; k < d; ++k) tp[(size_t)i * d + k] = (float)(H.lo[k] + rnd() * (H.hi[k] - H.lo[k]));
@@ -912,7 +931,7 @@ static gwn_status autotune(gwn_model_s* m) {
                   cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
                   ensure_workspace(m, nt, 0) == GWN_OK;
         // best of two timed runs after one untimed run (microseconds)
-        auto timed = [&](double b, double bl) -> double {
+        auto timed_on = [&](double b, double bl, const float* pts_d, int np, double* out_d) -> double {
             gwn_query_opts q3;
             gwn_default_query_opts(&q3);
             q3.beta = b;
@@ -920,13 +939,14 @@ static gwn_status autotune(gwn_model_s* m) {
             float best = 1e30f;
             for (int rep = 0; rep < 3 && ok; ++rep) {
                 ok = cudaEventRecord(e0, 0) == cudaSuccess &&
-                     gwn_enqueue_device(m, dt, GWN_F32, nt, wt, nullptr, nullptr, q3, 0, m->ws) == GWN_OK &&
+                     gwn_enqueue_device(m, pts_d, GWN_F32, np, out_d, nullptr, nullptr, q3, 0, m->ws) == GWN_OK &&
                      cudaEventRecord(e1, 0) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
                 float ms = 0;
                 if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, ms);
             }
             return 1e3 * best;
         };
+        auto timed = [&](double b, double bl) -> double { return timed_on(b, bl, dt, nt, wt); };
         double best_t = 1e300;
         if (ok_cands.size() > 1) {
             for (const auto& c : ok_cands) {
@@ -1025,6 +1045,7 @@ static gwn_status build_common(int dim, const void* prims, size_t n, const gwn_b
     m->dim = dim;
     m->opts = o;
     m->eval_order = o.order;
+    m->local_ratio = o.local_ratio > 0 ? o.local_ratio : 0.0;
     m->leaf_far = o.leaf_far < 0 ? (dim == 3 ? 1 : 0) : (o.leaf_far ? 1 : 0);
     m->n_primitives = (int64_t)n;
     gwn_status code = GWN_OK;
@@ -1094,6 +1115,8 @@ gwn_status gwn_query(gwn_model m, const void* points, int32_t dtype, int32_t mem
     if (qo.beta != 0.0 && !(qo.beta >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta must be >= 2");
     if (qo.beta_leaf != 0.0 && !(qo.beta_leaf >= 2.0)) return fail(GWN_ERR_INVALID_ARG, "beta_leaf must be >= 2");
     if (!(qo.repair_band >= 0.0 && qo.repair_band < 0.5)) return fail(GWN_ERR_INVALID_ARG, "repair_band must be in [0, 0.5)");
+    if (!(qo.local_ratio <= 0.0 || (qo.local_ratio >= 4.0 && qo.local_ratio < 1e6)))
+        return fail(GWN_ERR_INVALID_ARG, "local_ratio must be <= 0 or in [4, 1e6)");
     DeviceGuard g(m->device);
     std::lock_guard<std::mutex> lk(m->mu);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1267,6 +1290,7 @@ gwn_status gwn_last_query_stats(gwn_model m, int64_t* out) {
     for (int k = 0; k < 8; ++k) out[4 + k] = (int64_t)wk[k];
     out[14] = (int64_t)(c[8] + c[9]);  // pairs the full evaluator took (the rest came from the node tables)
     out[15] = (int64_t)wk[kWorkFastNodes];
+    out[18] = (int64_t)wk[kWorkLocal];
     if (m->profiled) {
         double a = 0, b = 0, f = 0;
         for (int ch = 0; ch < m->prof_chunks; ++ch) {
@@ -1302,6 +1326,7 @@ gwn_status gwn_model_info(gwn_model m, gwn_model_stats* s) {
     s->repair_band = m->opts.repair_band;
     s->order = m->opts.order;
     s->eval_order = m->eval_order;
+    s->local_ratio = m->dim == 3 ? m->local_ratio : 0.0;
     for (int k = 0; k < 3; ++k) {
         s->lo[k] = m->host.lo[k];
         s->hi[k] = m->host.hi[k];
@@ -1443,7 +1468,7 @@ gwn_status gwn_model_save(gwn_model m, const char* path) {
     const int32_t hdr[4] = {(int32_t)kModelVersion, m->dim, m->leaf_far, (int32_t)sizeof(gwn_build_opts)};
     const HostModel& H = m->host;
     const int32_t hm[5] = {H.dim, H.n_leaves, H.max_depth, m->bin_ppc, m->eval_order};
-    const double rf[2] = {m->repair_node_factor, m->repair_leaf_factor};
+    const double rf[3] = {m->repair_node_factor, m->repair_leaf_factor, m->local_ratio};
     bool ok = std::fwrite(kModelMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
               std::fwrite(&m->n_primitives, sizeof(m->n_primitives), 1, f) == 1 &&
               std::fwrite(&m->opts, sizeof(gwn_build_opts), 1, f) == 1 && std::fwrite(hm, sizeof(hm), 1, f) == 1 &&
@@ -1466,7 +1491,7 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
     }
     char magic[8] = {};
     int32_t hdr[4] = {}, hm[5] = {};
-    double rf[2] = {};
+    double rf[3] = {};
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kModelMagic, 8) == 0 &&
               std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == (int32_t)kModelVersion &&
               (hdr[1] == 2 || hdr[1] == 3) && hdr[3] == (int32_t)sizeof(gwn_build_opts) &&
@@ -1498,8 +1523,9 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out) {
         m->eval_order = hm[4];
         m->repair_node_factor = rf[0];
         m->repair_leaf_factor = rf[1];
+        m->local_ratio = rf[2];
         ok = hm[3] >= 1 && hm[3] <= 4096 && rf[0] >= 1.0 && rf[0] <= 16.0 && rf[1] >= 1.0 && rf[1] <= 16.0 &&
-             hm[4] >= 0 && hm[4] <= m->opts.order;
+             hm[4] >= 0 && hm[4] <= m->opts.order && (rf[2] == 0.0 || (rf[2] >= 4.0 && rf[2] < 1e6));
         // consistency of the arrays the kernels index
         ok = ok && host_model_consistent(H, m->dim);
     }

@@ -160,7 +160,8 @@ enum {
     kWorkHits = 6,       // foot-point searches (3D near leaves)
     kWorkChords = 7,     // chord angles (2D leaf pieces)
     kWorkFastNodes = 8,  // Gauss-Legendre nodes read from the node tables (leaf3_fast32)
-    kWorkCount = 9
+    kWorkLocal = 9,      // nodes and leaves taken by a packet's local expansion (k_trav3)
+    kWorkCount = 10
 };
 
 struct WorkLocal {
@@ -174,6 +175,7 @@ struct QueryParams {
     double beta2_repair;       // beta^2 of the FP64 repair pass; <= 0: direct sum
     double beta2_repair_leaf;  // beta^2 of the repair's leaf far test (3D)
     float band;                // repair band around half-integers
+    float kappa2;              // (packet local expansion ratio)^2; 0: off
     int mode;                  // GWN_MODE_*
     int precision;             // GWN_PREC_*
 };
@@ -224,6 +226,7 @@ struct Workspace {
     uint32_t* rst;    // n: status bits per repair-list entry
     int* gcount;      // [0] entries of rlist_g, [1] FP64 pairs of its pass, [2] of which the full evaluator
                       // takes (cleared once per query)
+    unsigned* bbox;   // 8: the chunk's bounding box as order-preserving keys (k_bbox)
     int rcap;         // entries of rlist_g (= the points a workspace holds)
     long long pair_cap;
 };

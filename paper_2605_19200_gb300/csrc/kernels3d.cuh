@@ -968,6 +968,75 @@ GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz, b
     return w;
 }
 
+// Second-order local expansion of one node's order-2 far field about a packet
+// centre p (an extension beyond the paper, for packets of nearby queries):
+// with D = x0 - p and s = q - p, F(x0 - q) = F(D - s) ~ F(D) - grad F(D) . s
+// + s^T H_F(D) s / 2.  F is the folded form t0 g3 + t1 g5 + t2 g7 (g_n =
+// |r|^-n, t_k the polynomials of far3_eval), so
+//   grad F = sum_k (g_n grad t_k - n g_{n+2} t_k r),
+//   H_F    = sum_k (g_n H t_k - n g_{n+2} (grad t_k r^T + r grad t_k^T)
+//                   + t_k (n (n+2) g_{n+4} r r^T - n g_{n+2} I)),  n = 3 + 2k.
+// v receives F, grad F (3) and H_F (xx yy zz xy xz yz).
+GWN_HD inline void far3_local2(const float4* M, float x, float y, float z, float v[10]) {
+    float f[24];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 a = GWN_LDG(M + k);
+        f[4 * k] = a.x; f[4 * k + 1] = a.y; f[4 * k + 2] = a.z; f[4 * k + 3] = a.w;
+    }
+    const float r2 = x * x + y * y + z * z;
+    const float rs = Num<float>::rsqrt_(r2), i2 = rs * rs;
+    float g[6];  // g3 .. g13 in steps of 2
+    g[0] = i2 * rs;
+#pragma unroll
+    for (int k = 1; k < 6; ++k) g[k] = g[k - 1] * i2;
+    const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    // the three polynomials with their gradients and Hessians
+    float t[3], gt[3][3], ht[3][6];
+    t[0] = f[0] * x + f[1] * y + f[2] * z + f[3];
+    gt[0][0] = f[0]; gt[0][1] = f[1]; gt[0][2] = f[2];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ht[0][k] = 0.f;
+    t[1] = f[4] * xx + f[5] * yy + f[6] * zz + f[7] * xy + f[8] * xz + f[9] * yz + f[10] * x + f[11] * y + f[12] * z;
+    gt[1][0] = 2.f * f[4] * x + f[7] * y + f[8] * z + f[10];
+    gt[1][1] = 2.f * f[5] * y + f[7] * x + f[9] * z + f[11];
+    gt[1][2] = 2.f * f[6] * z + f[8] * x + f[9] * y + f[12];
+    ht[1][0] = 2.f * f[4]; ht[1][1] = 2.f * f[5]; ht[1][2] = 2.f * f[6];
+    ht[1][3] = f[7]; ht[1][4] = f[8]; ht[1][5] = f[9];
+    t[2] = x * (f[13] * xx + f[16] * xy + f[17] * xz + f[18] * yy + f[20] * zz + f[22] * yz) +
+           y * (f[14] * yy + f[19] * yz + f[21] * zz) + f[15] * zz * z;
+    gt[2][0] = 3.f * f[13] * xx + 2.f * f[16] * xy + 2.f * f[17] * xz + f[18] * yy + f[20] * zz + f[22] * yz;
+    gt[2][1] = 3.f * f[14] * yy + f[16] * xx + 2.f * f[18] * xy + 2.f * f[19] * yz + f[21] * zz + f[22] * xz;
+    gt[2][2] = 3.f * f[15] * zz + f[17] * xx + f[19] * yy + 2.f * f[20] * xz + 2.f * f[21] * yz + f[22] * xy;
+    ht[2][0] = 6.f * f[13] * x + 2.f * f[16] * y + 2.f * f[17] * z;
+    ht[2][1] = 6.f * f[14] * y + 2.f * f[18] * x + 2.f * f[19] * z;
+    ht[2][2] = 6.f * f[15] * z + 2.f * f[20] * x + 2.f * f[21] * y;
+    ht[2][3] = 2.f * f[16] * x + 2.f * f[18] * y + f[22] * z;
+    ht[2][4] = 2.f * f[17] * x + 2.f * f[20] * z + f[22] * y;
+    ht[2][5] = 2.f * f[19] * y + 2.f * f[21] * z + f[22] * x;
+    const float r[3] = {x, y, z};
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float n = (float)(3 + 2 * k);
+        const float gn = g[k], gn2 = g[k + 1], gn4 = g[k + 2];
+        const float a = n * gn2, b = n * (n + 2.f) * gn4 * t[k];
+        v[0] += t[k] * gn;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[1 + c] += gt[k][c] * gn - a * t[k] * r[c];
+        // Hessian entries (i, j) in the order xx yy zz xy xz yz
+        const int I[6] = {0, 1, 2, 0, 0, 1}, J[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            const int i = I[e], j = J[e];
+            float h = ht[k][e] * gn - a * (gt[k][i] * r[j] + r[i] * gt[k][j]) + b * r[i] * r[j];
+            if (i == j) h -= a * t[k];
+            v[4 + e] += h;
+        }
+    }
+}
+
 // Algorithm 1 for one 3D query, FP32 (beta2l: the leaves' far test, <= 0 means beta2)
 GWN_HD float query3_32(const DevTree& t, float qx, float qy, float qz, float beta2, uint32_t& st, float beta2l = 0.f) {
     if (!(beta2l > 0.f)) beta2l = beta2;

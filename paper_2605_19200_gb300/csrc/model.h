@@ -29,6 +29,10 @@ struct gwn_model_s {
     // model built with order 3 may be evaluated at order 2 when the autotuner
     // finds that faster at the tolerance (the order-2 coefficients are the same)
     int eval_order = 2;
+    // packet local expansion of the 3D traversal: nodes beyond this many packet
+    // radii (and far for the whole packet box) are taken by a second-order local
+    // expansion about the packet's centre; 0: off (the default)
+    double local_ratio = 0.0;
     // automatic FP64 repair (beta_repair < 0, more than 512 leaves): its far
     // tests at these multiples of beta (nodes) and beta_leaf (leaves); the
     // autotuner lowers them while the repaired values stay within 1e-7

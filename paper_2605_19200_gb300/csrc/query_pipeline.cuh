@@ -70,14 +70,67 @@ __device__ __forceinline__ void load_point_f(const void* pts, int dtype, int dim
     }
 }
 
+// order-preserving integer key of a float (larger float, larger key) and back
+__device__ __forceinline__ unsigned float_key(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// bounding box of the n points: box[0..2] receive the complemented keys of the
+// minima and box[3..5] the keys of the maxima (box zeroed beforehand, so that
+// atomicMax serves both), one atomic per block and coordinate
 template <int DIM>
-__global__ void k_bin(const void* pts, int dtype, int n, float3 lo, float3 inv, int bits, int* key, int* hist) {
+__global__ void __launch_bounds__(128) k_bbox(const void* pts, int dtype, int n, unsigned* box) {
+    __shared__ unsigned sk[4][6];
+    const unsigned full = 0xffffffffu;
+    unsigned kmin[3] = {0u, 0u, 0u}, kmax[3] = {0u, 0u, 0u};  // complemented minima, maxima
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float q[3] = {0, 0, 0};
+        load_point_f(pts, dtype, DIM, i, q);
+        for (int k = 0; k < DIM; ++k) {
+            if (q[k] != q[k]) continue;  // NaN: no cell of its own
+            const unsigned key = float_key(q[k]);
+            kmin[k] = max(kmin[k], ~key);
+            kmax[k] = max(kmax[k], key);
+        }
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int off = 16; off > 0; off >>= 1) {
+            kmin[k] = max(kmin[k], __shfl_xor_sync(full, kmin[k], off));
+            kmax[k] = max(kmax[k], __shfl_xor_sync(full, kmax[k], off));
+        }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+            sk[warp][k] = kmin[k];
+            sk[warp][3 + k] = kmax[k];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        unsigned v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = max(v, sk[w][threadIdx.x]);
+        if (v) atomicMax(&box[threadIdx.x], v);
+    }
+}
+
+template <int DIM>
+__global__ void k_bin(const void* pts, int dtype, int n, const unsigned* box, int bits, int* key, int* hist) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float q[3] = {0, 0, 0};
     load_point_f(pts, dtype, DIM, i, q);
     const float cells = (float)(1 << bits);
-    float l[3] = {lo.x, lo.y, lo.z}, s[3] = {inv.x, inv.y, inv.z};
+    // the grid spans the chunk's own box (k_bbox), so that points gathered in a
+    // small part of the model's box still fall into many cells
+    float l[3] = {0.f, 0.f, 0.f}, s[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < DIM; ++k) {
+        l[k] = key_float(~box[k]);
+        const float e = key_float(box[3 + k]) - l[k];
+        s[k] = e > 0.f ? 1.f / e : 0.f;
+    }
     uint32_t c[3];
     for (int k = 0; k < DIM; ++k) {
         float t = (q[k] - l[k]) * s[k] * cells;
@@ -272,6 +325,197 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
             mask = (unsigned)e.y;
             __syncwarp();
         }
+    }
+    __syncwarp();
+    flush_warp_pairs(buf, own, bcnt, ws, ovf);
+    if ((ovf >> lane) & 1u) st |= kPairOverflow;
+    if (active) {
+        ws.wacc[qi] = w;
+        ws.st[qi] = st;
+        if (st & kPairOverflow) olist_out[atomicAdd(&ws.counters[3], 1)] = qi;
+    }
+    if (work) flush_work(wl, work);
+}
+
+// k_trav3 with the packet local expansion (order-2 models, query option
+// local_ratio; a local-expansion far field beyond the paper): the same walk,
+// and a node or leaf that every active lane of the packet needs, that passes
+// the far test for every point of the packet's box (|x0 - p| > beta r + rho,
+// p and rho the box's centre and half diagonal) and lies beyond kappa rho
+// (kappa2 = kappa^2) is not evaluated per lane: it goes to a per-warp list,
+// and 32 of them at a time each lane forms one node's second-order local
+// expansion about p (far3_local2), summed over the warp; every lane evaluates
+// the summed expansion at its own point at the end.  A kernel of its own:
+// sharing k_trav3's body cost the plain traversal 4 % (9.16 -> 9.51 ms on a
+// 2M-query model) at the same register count.
+template <int STACK>
+__global__ void __launch_bounds__(128) k_trav3_local(DevTree t, const void* pts, int dtype, int n, const int* perm,
+                                               float beta2, float beta2l, Workspace ws, unsigned long long* work,
+                                               const int* n_dev, int* olist_out, float kappa2) {
+    __shared__ int2 sstk[4][STACK];
+    __shared__ int2 sbuf[4][kPairBuf];
+    __shared__ unsigned char sown[4][kPairBuf];
+    __shared__ int slocal[4][32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int2* stk = sstk[threadIdx.x >> 5];
+    int2* buf = sbuf[threadIdx.x >> 5];
+    unsigned char* own = sown[threadIdx.x >> 5];
+    int* lst = slocal[threadIdx.x >> 5];
+    WorkLocal wl = {};
+    if (n_dev) n = *n_dev;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev && blockIdx.x * blockDim.x >= n) return;  // whole block past the list
+    const bool active = i < n;
+    int qi = active ? (perm ? perm[i] : i) : 0;
+    float q[3] = {0, 0, 0};
+    if (active) load_point_f(pts, dtype, 3, qi, q);
+    float w = 0.f;
+    uint32_t st = 0;
+    int bcnt = 0;                      // warp-uniform: entries in buf
+    unsigned ovf = 0;                  // lanes with pairs that did not fit the list
+    int sp = 0;                        // warp-uniform
+    const unsigned amask = __ballot_sync(full, active);
+
+    // packet box of the active lanes (centre p, half diagonal rho) and the
+    // local expansion's coefficients (F, grad F, Hessian), the same in all lanes
+    float pc[3] = {0.f, 0.f, 0.f}, rho = 0.f, lc[10];
+    int lcnt = 0;  // warp-uniform: entries in lst
+    {
+        float d2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float lo = active ? q[k] : 3.0e38f, hi = active ? q[k] : -3.0e38f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(full, lo, off));
+                hi = fmaxf(hi, __shfl_xor_sync(full, hi, off));
+            }
+            pc[k] = 0.5f * (lo + hi);
+            d2 += (hi - lo) * (hi - lo);
+        }
+        rho = 0.5f * sqrtf(d2);
+#pragma unroll
+        for (int k = 0; k < 10; ++k) lc[k] = 0.f;
+    }
+    // every lane takes one listed node's expansion, and the warp sums them
+    auto flush_local = [&]() {
+        float v[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) v[k] = 0.f;
+        __syncwarp();
+        if (lane < lcnt) {
+            const int c = lst[lane];
+            const float4 h = c < 0 ? GWN_LDG(t.lhdr + ~c) : GWN_LDG(t.hdr + c);
+            const float4* M = c < 0 ? t.lmom + (size_t)(~c) * kMom3Vec : t.mom + (size_t)c * kMom3Vec;
+            far3_local2(M, h.x - pc[0], h.y - pc[1], h.z - pc[2], v);
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(full, v[k], off);
+            lc[k] += v[k];
+        }
+        lcnt = 0;
+        __syncwarp();
+    };
+    // c is far for the whole packet box and beyond kappa rho: list it (true)
+    auto packet_far = [&](int c, unsigned msk, const float4& h, float b2) -> bool {
+        if (msk != amask) return false;
+        const float dx = h.x - pc[0], dy = h.y - pc[1], dz = h.z - pc[2];
+        const float dd = dx * dx + dy * dy + dz * dz;
+        const float lim = sqrtf(b2 * h.w) + rho;
+        if (!(dd > kappa2 * rho * rho && dd > lim * lim)) return false;
+        if (lane == 0) lst[lcnt] = c;
+        if (work && ((amask >> lane) & 1u)) wl.v[kWorkLocal] += 1;
+        if (++lcnt == 32) flush_local();
+        return true;
+    };
+
+    // Test node or leaf c for the lanes of `msk` (warp-uniform c and msk):
+    // Taylor terms for the far lanes, pairs for the lanes that need a leaf
+    // exactly; returns the lanes for which an internal c is near.
+    auto test = [&](int c, unsigned msk) -> unsigned {
+        const bool mine = (msk >> lane) & 1u;
+        if (c < 0) {
+            const int li = ~c;
+            const float4 h = GWN_LDG(t.lhdr + li);
+            if (work && mine) wl.v[kWorkLeafTests] += 1;
+            if (t.leaf_far && packet_far(c, msk, h, beta2l)) return 0u;
+            const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
+            const bool far = mine && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2l * h.w;
+            if (far) {
+                if (work) wl.v[kWorkFar] += 1;
+                w += far3_node32(t.lmom + (size_t)li * kMom3Vec, rx, ry, rz, false);
+            }
+            const unsigned need = __ballot_sync(full, mine && !far);
+            if (need) {
+                const int nn = __popc(need);
+                if (bcnt + nn > kPairBuf) {
+                    __syncwarp();
+                    flush_warp_pairs(buf, own, bcnt, ws, ovf);
+                    bcnt = 0;
+                    __syncwarp();
+                }
+                if ((need >> lane) & 1u) {
+                    const int pos = bcnt + __popc(need & ((1u << lane) - 1u));
+                    buf[pos] = make_int2(qi, li);
+                    own[pos] = (unsigned char)lane;
+                }
+                bcnt += nn;
+            }
+            return 0u;
+        }
+        const float4 h = GWN_LDG(t.hdr + c);
+        if (work && mine) wl.v[kWorkNodes] += 1;
+        if (packet_far(c, msk, h, beta2)) return 0u;
+        const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
+        const bool far = mine && rx * rx + ry * ry + rz * rz > beta2 * h.w;
+        if (far) {
+            if (work) wl.v[kWorkFar] += 1;
+            w += far3_node32(t.mom + (size_t)c * kMom3Vec, rx, ry, rz, false);
+        }
+        return __ballot_sync(full, mine && !far);
+    };
+
+    int node = t.root;  // warp-uniform
+    unsigned mask = __ballot_sync(full, active);
+    if (mask) mask = test(node, mask);  // the root itself (a leaf when the model has one)
+    while (mask) {
+        const int2 ch = GWN_LDG(t.child + node);
+        const unsigned na = test(ch.x, mask);
+        const unsigned nb = test(ch.y, mask);
+        if (na) {
+            if (nb) {
+                if (sp < STACK) {
+                    if (lane == 0) stk[sp] = make_int2(ch.y, (int)nb);
+                    ++sp;
+                } else if ((nb >> lane) & 1u) {
+                    st |= GWN_QS_STACK_OVERFLOW;  // the second subtree is dropped for these lanes
+                }
+                __syncwarp();
+            }
+            node = ch.x;
+            mask = na;
+        } else if (nb) {
+            node = ch.y;
+            mask = nb;
+        } else {
+            if (sp == 0) break;
+            --sp;
+            const int2 e = stk[sp];
+            node = e.x;
+            mask = (unsigned)e.y;
+            __syncwarp();
+        }
+    }
+    {
+        if (lcnt > 0) flush_local();
+        // F(D - s) ~ F - grad F . s + s^T H s / 2, s = q - p
+        const float sx = q[0] - pc[0], sy = q[1] - pc[1], sz = q[2] - pc[2];
+        w += lc[0] - (lc[1] * sx + lc[2] * sy + lc[3] * sz) +
+             0.5f * (lc[4] * sx * sx + lc[5] * sy * sy + lc[6] * sz * sz) + lc[7] * sx * sy + lc[8] * sx * sz +
+             lc[9] * sy * sz;
     }
     __syncwarp();
     flush_warp_pairs(buf, own, bcnt, ws, ovf);

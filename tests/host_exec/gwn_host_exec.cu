@@ -196,3 +196,28 @@ extern "C" int hx_leaf_paths64(const gwn_patch3d* patches, size_t n, const gwn_b
         }
     return t.n_leaves;
 }
+
+// The packet local expansion of internal node `node` about the point p
+// (far3_local2) evaluated at p + s[k], and the node's own FP32 Taylor term at
+// the same points (far3_node32), for ns offsets.  Returns the node count, or -1.
+extern "C" int hx_local2(const gwn_patch3d* patches, size_t n, const gwn_build_opts* o, int node, const double* p,
+                         const double* s, int ns, double* local, double* direct) {
+    init_tables();
+    HostModel H;
+    gwn_status code;
+    if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
+    const DevTree t = host_tree(H, 1, o->order);
+    if (node < 0 || node >= t.n_internal) return -1;
+    const float4 h = t.hdr[node];
+    const float4* M = t.mom + (size_t)node * kMom3Vec;
+    const float D[3] = {h.x - (float)p[0], h.y - (float)p[1], h.z - (float)p[2]};
+    float v[10];
+    far3_local2(M, D[0], D[1], D[2], v);
+    for (int k = 0; k < ns; ++k) {
+        const float sx = (float)s[3 * k], sy = (float)s[3 * k + 1], sz = (float)s[3 * k + 2];
+        local[k] = v[0] - (v[1] * sx + v[2] * sy + v[3] * sz) + 0.5f * (v[4] * sx * sx + v[5] * sy * sy + v[6] * sz * sz) +
+                   v[7] * sx * sy + v[8] * sx * sz + v[9] * sy * sz;
+        direct[k] = far3_node32(M, D[0] - sx, D[1] - sy, D[2] - sz, false);
+    }
+    return t.n_internal;
+}

@@ -23,7 +23,7 @@ from synth import configs
 
 def _arrays(path):
     data = open(path, "rb").read()
-    head = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 20 + 16 + 48
+    head = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 20 + 24 + 48
     return data[:8 + 16 + 8], data[head:]
 
 

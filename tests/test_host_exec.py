@@ -17,6 +17,7 @@ import subprocess
 import numpy as np
 import pytest
 
+import paper_2605_19200_gb300 as gwn
 from paper_2605_19200_gb300 import api
 from synth import configs
 from synth import geometry as G
@@ -50,6 +51,8 @@ def hx():
                                    P, P, P, ctypes.c_int]
     lib.hx_leaf_paths64.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), P, ctypes.c_int,
                                     P, P, ctypes.c_int]
+    lib.hx_local2.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(api.gwn_build_opts), ctypes.c_int, P, P,
+                              ctypes.c_int, P, P]
     return lib
 
 
@@ -414,3 +417,35 @@ def test_order3_far_field_error_law(hx, oracle_lib):
         else:
             assert e[(3, 4.0)] <= e[(2, 4.0)], e
         assert e[(3, 4.0)] < 1e-4, e
+
+
+def test_packet_local_expansion_matches_the_node_term(hx):
+    """The packet local expansion (far3_local2; a local-expansion far field, one
+    step beyond the paper's per-query terms): for a node seen from a packet
+    centre p at 12 node radii, its second-order expansion about p evaluated at
+    p + s equals the node's own Taylor term at p + s up to a remainder that
+    falls like |s|^3 -- about 8x per halving of |s| -- and stays below 2e-3 of
+    the term at |s| = |D| / 16."""
+    patches, _ = configs.cad_3d(1234, 120, 0)
+    parr, keep = api.marshal_patches(patches)
+    o = _hopts(beta=6.0, beta_leaf=4.0)
+    m = gwn.gwn_build_3d(patches, device=-2, beta=6.0, beta_leaf=4.0)
+    tr = m.tree()
+    rng = np.random.default_rng(3)
+    for node in (0, 3, 17, 60):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        D = 12.0 * max(tr["r"][node], 0.05) * u
+        p = np.ascontiguousarray(tr["x0"][node] - D)
+        dirs = rng.normal(size=(8, 3))
+        dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+        errs = []
+        for frac in (1 / 8, 1 / 16):
+            sv = np.ascontiguousarray(dirs * frac * np.linalg.norm(D))
+            loc, dr = np.zeros(8), np.zeros(8)
+            assert hx.hx_local2(ctypes.cast(parr, ctypes.c_void_p), len(patches), ctypes.byref(o), node,
+                                p.ctypes.data, sv.ctypes.data, 8, loc.ctypes.data, dr.ctypes.data) > node
+            scale = np.max(np.abs(dr))
+            errs.append(np.max(np.abs(loc - dr)) / scale)
+        assert errs[1] < 2e-3, (node, errs)
+        assert errs[1] < errs[0] / 5, (node, errs)   # third-order remainder: ~1/8 per halving

@@ -327,8 +327,8 @@ def _split_model_file(data):
     """(header bytes, [(name, count, payload bytes)]) of a model file."""
     import ctypes
     from paper_2605_19200_gb300 import api
-    # magic, 4 int32, primitive count, options, 5 int32 (tree header, binning, order), 2 repair factors, box
-    off = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 20 + 16 + 48
+    # magic, 4 int32, primitive count, options, 5 int32 (tree header, binning, order), 3 doubles (repair factors, local ratio), box
+    off = 8 + 16 + 8 + ctypes.sizeof(api.gwn_build_opts) + 20 + 24 + 48
     head, arrays = data[:off], []
     for name, es in _ARRAY_ELEM:
         n = int(np.frombuffer(data[off:off + 8], dtype=np.uint64)[0])

@@ -354,7 +354,7 @@ def main():
                     help="packet local expansion ratio of the models (<= 0: off, the default)")
     ap.add_argument("--tree-builder", type=int, default=-1, choices=[-1, 0, 1],
                     help="0: Karras LBVH; 1: top-down sweep; -1: the library's default (1)")
-    ap.add_argument("--order", type=int, default=2, choices=[2, 3],
+    ap.add_argument("--order", type=int, default=3, choices=[2, 3],
                     help="Taylor order of the models' build (3: the autotuner picks order 2 or 3 per model)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the single-model configurations 1-3")

@@ -104,7 +104,9 @@ typedef struct {
     int32_t order;        /* Taylor order 0, 1 or 2 of Eq. 3 (default 2); 3D models also take 3, the next
                              term of the same expansion (third-order moments int y y y n), beyond the
                              paper: its remainder falls one power of r/|x0 - q| faster, so the same
-                             tolerance holds at a smaller beta and beta_leaf */
+                             tolerance holds at a smaller beta and beta_leaf.  The FP64 evaluations (the
+                             repair, GWN_PREC_FP64) then always take the order-3 terms; the FP32 bulk
+                             takes them where the autotuner finds that faster (gwn_model_stats.eval_order) */
     double beta;          /* far test ||q - c|| > beta * r, r = half box diagonal; >= 2, or 0 = autotune:
                              among the (beta, beta_leaf) pairs whose FP32 error on validation points
                              (FP64 direct sum on the device) stays below tolerance / 2, the fastest on

@@ -181,12 +181,26 @@ gwn_status upload_model(gwn_model_s* m) {
 #define UP(vec, field) if ((s = upload(m, H.vec, &t.field)) != GWN_OK) return s
     t.leaf_far = m->leaf_far;
     t.order3 = H.dim == 3 && m->eval_order >= 3 ? 1 : 0;
+    t.order3_64 = H.dim == 3 && m->opts.order >= 3 ? 1 : 0;
     UP(lhdr, lhdr);
     UP(lmom, lmom);
     UP(lhdr64, lhdr64);
     UP(lmom64, lmom64);
     UP(hdr, hdr);
     UP(child, child);
+    {
+        // both children's headers beside each internal node (3D traversal): the
+        // child indices and the headers load together instead of one after the other
+        std::vector<float4> chdr;
+        if (H.dim == 3) {
+            chdr.resize(H.child.size() * 2);
+            for (size_t k = 0; k < H.child.size(); ++k) {
+                const int c[2] = {H.child[k].x, H.child[k].y};
+                for (int j = 0; j < 2; ++j) chdr[2 * k + j] = c[j] < 0 ? H.lhdr[~c[j]] : H.hdr[c[j]];
+            }
+        }
+        if ((s = upload(m, chdr, &t.chdr)) != GWN_OK) return s;
+    }
     UP(mom, mom);
     UP(hdr64, hdr64);
     UP(mom64, mom64);
@@ -989,7 +1003,7 @@ static gwn_status autotune(gwn_model_s* m) {
     // node and leaf factors are lowered from 3 while its values stay within 1e-7
     // of the FP64 direct sum; fewer FP64 pairs per repaired point.
     if (d == 3 && m->opts.beta_repair < 0 && H.n_leaves > 512 && m->opts.precision == GWN_PREC_FP32_REPAIR) {
-        const double facs[][2] = {{3.0, 3.0}, {2.5, 2.5}, {2.5, 2.0}, {2.0, 2.0}, {2.0, 1.5}};
+        const double facs[][2] = {{3.0, 3.0}, {2.5, 2.5}, {2.5, 2.0}, {2.0, 2.0}, {2.0, 1.5}, {1.5, 1.5}};
         uint32_t* dst = nullptr;
         int* dcnt = nullptr;
         bool ok = cudaMalloc(&dst, nv * sizeof(uint32_t)) == cudaSuccess && cudaMalloc(&dcnt, sizeof(int)) == cudaSuccess;

@@ -117,7 +117,9 @@ struct DevTree {
     int n_internal;
     int root;                  // 0, or ~0 when the model has a single leaf
     int leaf_far;              // 1: leaves also take the far test (their own moments)
-    int order3;                // 1: 3D moment blocks carry the order-3 terms (kMom3Vec float4 read)
+    int order3;                // 1: the FP32 traversal evaluates the order-3 terms
+    int order3_64;             // 1: the FP64 evaluations (repair, FP64 precision) evaluate them: every
+                               // model built with order 3, whatever order its FP32 bulk evaluates
     // per-leaf far-field data (same layout as the nodes)
     const float4* lhdr;
     const float4* lmom;
@@ -126,6 +128,7 @@ struct DevTree {
     // internal nodes
     const float4* hdr;         // (x0.x, x0.y, x0.z, r^2)
     const int2* child;
+    const float4* chdr;        // 3D: 2 per internal node, the headers of its two children (hdr or lhdr)
     const float4* mom;         // kMom2Vec or kMom3Vec per node
     const double* hdr64;       // 4 per node
     const double* mom64;       // kMom2F64 or kMom3F64 per node

@@ -1094,7 +1094,7 @@ GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, doubl
                 const double* h = t.lhdr64 + (size_t)li * 4;
                 double rx = h[0] - qx, ry = h[1] - qy, rz = h[2] - qz;
                 if (rx * rx + ry * ry + rz * rz > beta2 * h[3]) {
-                    w += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz, t.order3);
+                    w += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz, t.order3_64);
                     done = true;
                 }
             }
@@ -1103,7 +1103,7 @@ GWN_HD double query3_64(const DevTree& t, double qx, double qy, double qz, doubl
             const double* h = t.hdr64 + (size_t)node * 4;
             double rx = h[0] - qx, ry = h[1] - qy, rz = h[2] - qz;
             if (rx * rx + ry * ry + rz * rz > beta2 * h[3]) {
-                w += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz, t.order3);
+                w += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz, t.order3_64);
             } else {
                 int2 ch = t.child[node];
                 if (sp < kStack64) stack[sp++] = ch.y; else st |= GWN_QS_UNRESOLVED;

@@ -254,11 +254,10 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
     // Test node or leaf c for the lanes of `msk` (warp-uniform c and msk):
     // Taylor terms for the far lanes, pairs for the lanes that need a leaf
     // exactly; returns the lanes for which an internal c is near.
-    auto test = [&](int c, unsigned msk) -> unsigned {
+    auto test = [&](int c, unsigned msk, const float4& h) -> unsigned {
         const bool mine = (msk >> lane) & 1u;
         if (c < 0) {
             const int li = ~c;
-            const float4 h = GWN_LDG(t.lhdr + li);
             const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
             const bool far = mine && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2l * h.w;
             if (work && mine) wl.v[kWorkLeafTests] += 1;
@@ -284,7 +283,6 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
             }
             return 0u;
         }
-        const float4 h = GWN_LDG(t.hdr + c);
         const float rx = h.x - q[0], ry = h.y - q[1], rz = h.z - q[2];
         const bool far = mine && rx * rx + ry * ry + rz * rz > beta2 * h.w;
         if (work && mine) wl.v[kWorkNodes] += 1;
@@ -297,11 +295,13 @@ __global__ void __launch_bounds__(128) k_trav3(DevTree t, const void* pts, int d
 
     int node = t.root;  // warp-uniform
     unsigned mask = __ballot_sync(full, active);
-    if (mask) mask = test(node, mask);  // the root itself (a leaf when the model has one)
+    if (mask) mask = test(node, mask, node < 0 ? GWN_LDG(t.lhdr + ~node) : GWN_LDG(t.hdr + node));  // the root
     while (mask) {
+        // the child indices and both children's headers, loaded together
         const int2 ch = GWN_LDG(t.child + node);
-        const unsigned na = test(ch.x, mask);
-        const unsigned nb = test(ch.y, mask);
+        const float4 ha = GWN_LDG(t.chdr + 2 * node), hb = GWN_LDG(t.chdr + 2 * node + 1);
+        const unsigned na = test(ch.x, mask, ha);
+        const unsigned nb = test(ch.y, mask, hb);
         if (na) {
             if (nb) {
                 if (sp < STACK) {
@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
                         const double* h = t.lhdr64 + (size_t)li * 4;
                         double rx = h[0] - q[0], ry = h[1] - q[1], rz = h[2] - q[2];
                         if (beta2rl > 0 && t.leaf_far && rx * rx + ry * ry + rz * rz > beta2rl * h[3]) {
-                            acc += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz, t.order3);
+                            acc += far3_eval<double>(t.lmom64 + (size_t)li * kMom3F64, rx, ry, rz, t.order3_64);
                         } else {
                             int slot = atomicAdd(R.npairs, 1);
                             if (slot < kRepairPairCap) R.pairs[slot] = make_int2(k, li);
@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(32 * kRepairWarps) k_rtrav_warp(DevTree t, con
                     double d2 = rx * rx + ry * ry + rz * rz;
                     if (beta2r > 0 && d2 > beta2r * h[3]) {
                         if (DIM == 2) acc += far2_eval<double>(t.mom64 + (size_t)node * kMom2F64, rx, ry);
-                        else acc += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz, t.order3);
+                        else acc += far3_eval<double>(t.mom64 + (size_t)node * kMom3F64, rx, ry, rz, t.order3_64);
                     } else {
                         int2 ch = t.child[node];
                         c0 = ch.x;

@@ -59,6 +59,7 @@ DevTree host_tree(const HostModel& H, int leaf_far, int order = 2) {
     t.root = H.n_leaves > 1 ? 0 : ~0;
     t.leaf_far = leaf_far;
     t.order3 = H.dim == 3 && order >= 3 ? 1 : 0;
+    t.order3_64 = t.order3;
     t.lhdr = H.lhdr.data();
     t.lmom = H.lmom.data();
     t.lhdr64 = H.lhdr64.data();

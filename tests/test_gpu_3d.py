@@ -117,11 +117,14 @@ def test_sphere_near_surface(oracle_lib):
     assert np.array_equal(np.round(w[ok]), np.round(w_ref[ok]))
 
 
-def test_cad_model_fp32_and_direct(oracle_lib):
+@pytest.mark.parametrize("tree_builder", [1, 0])
+def test_cad_model_fp32_and_direct(oracle_lib, tree_builder):
+    """A CAD solid through the FP32 traversal over either hierarchy (top-down
+    sweep, Karras LBVH) and through the plain FP32 direct sum, against the oracle."""
     patches, q = configs.cad_3d(1234, 400, 4000)
     w_ref, fl = oracle_lib.gwn3d(patches, q[:600], near_thr=1e-6 * _diag(patches))
     ok = np.isfinite(w_ref)
-    m = gwn.gwn_build_3d(patches, beta=6.0)
+    m = gwn.gwn_build_3d(patches, beta=6.0, tree_builder=tree_builder)
     w, lab, st = m.query(_q(q))
     w = w.cpu().numpy()[:600]
     assert np.max(np.abs(w[ok] - w_ref[ok])) <= 1e-4

@@ -247,7 +247,7 @@ typedef struct {
     int32_t device;         /* CUDA ordinal holding the model, or GWN_DEVICE_HOST_ONLY */
     int32_t bin_points_per_cell; /* 3D: points per Morton cell the query's spatial binning aims at (a chunk
                                of n points is binned with round(log2(n / this) / 3) bits per axis, 3..6);
-                               picked by the autotuner from 4, 16, 64 by measured time (default 16).
+                               picked by the autotuner from 4, 8, 16, 32, 64 by measured time (default 16).
                                2D: 0 (9 bits per axis) */
     int32_t stack_depth;    /* warp-stack entries of the packet traversal (from the tree depth) */
     double beta_repair_leaf; /* far-test factor of the FP64 repair's leaves (0: exact sum over every leaf) */

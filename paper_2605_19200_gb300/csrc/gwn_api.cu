@@ -829,9 +829,9 @@ static gwn_status autotune(gwn_model_s* m) {
     qo.mode = GWN_MODE_DIRECT;
     qo.precision = GWN_PREC_FP64;
     if (s == GWN_OK) s = gwn_enqueue_device(m, dp, GWN_F32, nv, ref, nullptr, nullptr, qo, 0, m->ws);
-    const double betas[] = {3.0, 3.5, 4.0, 5.0, 6.0, 8.0, 10.0, 12.0, 16.0};
+    const double betas[] = {3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0, 7.0, 8.0, 10.0, 12.0, 16.0};
     // 2D leaves have no separate factor (0 = beta); 3D leaves: per-level factors
-    const double leafb[] = {0.0, 2.0, 2.5, 3.0, 3.5, 4.0, 5.0};
+    const double leafb[] = {0.0, 2.0, 2.5, 2.75, 3.0, 3.25, 3.5, 4.0, 5.0};
     double best_cost = 1e300, best_b = 0, best_bl = 0;
     int best_o = m->eval_order;
     std::vector<std::tuple<double, double, double, int>> ok_cands;  // (counted flops, beta, beta_leaf, order)
@@ -982,7 +982,7 @@ static gwn_status autotune(gwn_model_s* m) {
             const double bl = m->opts.beta_leaf > 0 ? m->opts.beta_leaf : m->opts.beta;
             int best_ppc = m->bin_ppc;
             double bt = 1e300;
-            for (int ppc : {4, 16, 64}) {
+            for (int ppc : {4, 8, 16, 32, 64}) {
                 m->bin_ppc = ppc;
                 const double tus = timed(m->opts.beta, bl);
                 if (ok && tus < bt) {

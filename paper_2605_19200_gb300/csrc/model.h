@@ -20,7 +20,7 @@ struct gwn_model_s {
     gwn_build_opts opts{};
     // launch parameters of the 3D query: the spatial binning aims at this many
     // points per Morton cell (a chunk of n points gets 3 log2(n / ppc) / 3 bits,
-    // 3..6 per axis; picked by the autotuner from 4, 16, 64 by measured time),
+    // 3..6 per axis; picked by the autotuner from 4, 8, 16, 32, 64 by measured time),
     // and the packet traversal's warp stack (64, 96 or 128 entries, from the
     // tree depth)
     int bin_ppc = 16;

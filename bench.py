@@ -358,7 +358,7 @@ def main():
                     help="Taylor order of the models' build (3: the autotuner picks order 2 or 3 per model)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the single-model configurations 1-3")
-    ap.add_argument("--streams", type=int, default=8,
+    ap.add_argument("--streams", type=int, default=16,
                     help="streams of the batched query (one graph launch per step); 0 = one gwn_query per model")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of each serving phase")
     ap.add_argument("--kernels-only", action="store_true",

@@ -609,10 +609,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_serve:
         serving = serving_leg(gwn, args.serve_seconds, log)
 
-    # kernels per chunk of up to 2^19 points: box, bin, scan, scatter; 3 rounds of traversal, pair histogram,
+    # kernels per chunk of up to 2^20 points: box, bin, scan, scatter; 3 rounds of traversal, pair histogram,
     # scan, pair sort, node-table pairs, full pairs (+ round switch x2); near band, overflow, finish, the
     # chunk's own repair x4 (normally empty), counter accumulate; per query: repair x4 + its accumulate
-    launches_per_step = sum(32 * math.ceil(p.shape[0] / (1 << 19)) + 5 for p in points)
+    launches_per_step = sum(32 * math.ceil(p.shape[0] / (1 << 20)) + 5 for p in points)
     line = {
         "metric": "GWN queries/s (batched containment, 16 trimmed-NURBS models)",
         "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),

@@ -432,7 +432,7 @@ size_t workspace_layout(int dim, int n_leaves, size_t n, char* base, Workspace* 
     return off;
 }
 
-constexpr size_t kChunk = (size_t)1 << 19;  // points per pass of the query pipeline
+constexpr size_t kChunk = (size_t)1 << 20;  // points per pass of the query pipeline
 constexpr int kQueryStats = 20;              // entries of gwn_last_query_stats
 
 // beta of the FP64 repair when the build leaves it automatic: the exact sum over
@@ -917,9 +917,10 @@ static gwn_status autotune(gwn_model_s* m) {
     // Counted flops do not weigh the kernels alike (the traversal's far tests and
     // Taylor terms issue about twice the instructions per counted flop of the
     // node-table leaves), so among the accurate candidates the cheapest four by
-    // count of each order are timed on 2^19 points uniform in the model's box (a
-    // full chunk of a large query: smaller samples bin and pair differently and
-    // flipped the choice between close candidates from run to run), and
+    // count of each order are timed on one chunk of points uniform in the model's
+    // box (binned and paired as a large query is: smaller samples bin and pair
+    // differently and flipped the choice between close candidates from run to
+    // run), and
     // the fastest is kept; then the binning's target points per cell is timed
     // the same way (the sample is binned at the resolution its size gives, as a
     // query is).
@@ -932,7 +933,7 @@ static gwn_status autotune(gwn_model_s* m) {
                 if (per_order[std::get<3>(c)]++ < 4) keep.push_back(c);
             ok_cands.swap(keep);
         }
-        const int nt = 1 << 19;  // one full chunk: binned and paired as a large query is
+        const int nt = (int)kChunk;  // one full chunk: binned and paired as a large query is
         std::vector<float> tp((size_t)nt * d);
         for (int i = 0; i < nt; ++i)
             for (int k = 0; k < d; ++k) tp[(size_t)i * d + k] = (float)(H.lo[k] + rnd() * (H.hi[k] - H.lo[k]));

@@ -163,20 +163,20 @@ def test_loops_full_grid_against_exact_reference(loops, oracle_lib):
 def test_repair_list_overflow_into_chunk_lists(star_ref):
     """A query's points to repair go to one query-wide list, repaired in a
     single pass after its last chunk; the list holds as many points as a chunk.
-    With 600,000 queries (two chunks) and a repair band of 0.4999 nearly every
+    With 1,200,000 queries (two chunks of up to 2^20) and a repair band of 0.4999 nearly every
     point is repaired, so the list overflows and the second chunk's remainder
     is repaired right after that chunk: every value must still be the FP64
     direct sum (2D repair without a far field: beta_repair = 0)."""
     curves, _ = configs.star_2d(n_queries=4)
     lo, hi = G.shape_bbox_2d(curves)
     rng = np.random.default_rng(600)
-    q = configs.uniform_queries(lo, hi, 600_000, rng, scale=1.2).astype(np.float32)
+    q = configs.uniform_queries(lo, hi, 1_200_000, rng, scale=1.2).astype(np.float32)
     m = gwn.gwn_build_2d(curves, beta=8.0, repair_band=0.4999, beta_repair=0.0)
     pts = torch.from_numpy(q).cuda()
     w, lab, st = m.query(pts)
     w64, _, _ = m.query(pts, mode=gwn.MODE_DIRECT, precision=gwn.PREC_FP64)
     st = st.cpu().numpy()
     rep = (st & gwn.QS_REPAIRED) != 0
-    assert rep.sum() > 524288                     # more than the query-wide list holds
+    assert rep.sum() > 1 << 20                    # more than the query-wide list holds
     np.testing.assert_allclose(w.cpu().numpy()[rep], w64.cpu().numpy()[rep], rtol=0, atol=1e-9)
     assert np.max(np.abs(w.cpu().numpy() - w64.cpu().numpy())) <= 1e-4

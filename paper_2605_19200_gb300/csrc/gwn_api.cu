@@ -681,17 +681,21 @@ static gwn_status enqueue_chunk(gwn_model_s* m, const void* pts, int dtype, size
 }
 
 // Enqueue a query on `st` for device-resident points and outputs, in chunks of
-// at most kChunk points (the workspace holds one chunk).
+// at most kChunk points (the workspace holds one chunk), or of max_chunk when
+// smaller: the serving loop takes shorter kernels so that requests on other
+// slots interleave.
 gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
-                              uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const Workspace& ws) {
+                              uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const Workspace& ws,
+                              size_t max_chunk) {
+    const size_t chunk = max_chunk > 0 ? std::min(max_chunk, kChunk) : kChunk;
     const size_t esz = (dtype == GWN_F32 ? sizeof(float) : sizeof(double)) * m->dim;
     GWN_CUDA_TRY(cudaMemsetAsync(ws.acc, 0, kCounterCount * sizeof(unsigned long long), st));
     if (qo.count_work) GWN_CUDA_TRY(cudaMemsetAsync(ws.work, 0, kWorkCount * sizeof(unsigned long long), st));
     m->prof_chunks = 0;
     m->profiled = qo.profile != 0;
     GWN_CUDA_TRY(cudaMemsetAsync(ws.gcount, 0, 8 * sizeof(int), st));
-    for (size_t off = 0; off < n; off += kChunk) {
-        size_t c = std::min(kChunk, n - off);
+    for (size_t off = 0; off < n; off += chunk) {
+        size_t c = std::min(chunk, n - off);
         gwn_status s = enqueue_chunk(m, reinterpret_cast<const char*>(pts) + off * esz, dtype, c, off, out_w + off,
                                      out_label ? out_label + off : nullptr, out_status ? out_status + off : nullptr,
                                      qo, st, ws);

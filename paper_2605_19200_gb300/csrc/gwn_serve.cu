@@ -144,7 +144,10 @@ gwn_status launch(gwn_server_s* S, Slot& sl, Request& r) {
         return gwn_fail(GWN_ERR_CUDA, "serve: copy in");
     gwn_query_opts qo;
     gwn_default_query_opts(&qo);
-    st = gwn_enqueue_device(S->models[r.model], dpts, r.dtype, r.n, dw, dl, nullptr, qo, sl.stream, sl.ws);
+    // chunks of 2^19 points: shorter kernels let the other slots' requests interleave
+    // (with full 2^20-point chunks the p99 at 0.9 of saturation doubled)
+    st = gwn_enqueue_device(S->models[r.model], dpts, r.dtype, r.n, dw, dl, nullptr, qo, sl.stream, sl.ws,
+                            (size_t)1 << 19);
     if (st != GWN_OK) return st;
     if (cudaMemcpyAsync(sl.pin_out, dw, ob, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
         cudaFreeAsync(sl.dev, sl.stream) != cudaSuccess)

@@ -66,9 +66,11 @@ struct gwn_model_s {
 // Record an error message for gwn_last_error() and return the status.
 gwn_status gwn_fail(gwn_status s, const std::string& msg);
 
-// Enqueue a query (device-resident points and outputs) on `st` using workspace `ws`.
+// Enqueue a query (device-resident points and outputs) on `st` using workspace `ws`,
+// in chunks of at most max_chunk points (0: the workspace's full chunk).
 gwn_status gwn_enqueue_device(gwn_model_s* m, const void* pts, int dtype, size_t n, double* out_w, int* out_label,
-                              uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const gwn::Workspace& ws);
+                              uint32_t* out_status, const gwn_query_opts& qo, cudaStream_t st, const gwn::Workspace& ws,
+                              size_t max_chunk = 0);
 
 // Bytes of a query workspace for `dim` (0 = either dimension) and `n_leaves`;
 // when base != nullptr also lays it out in the allocation at base.

@@ -1398,7 +1398,7 @@ gwn_status gwn_model_tree(gwn_model m, int32_t* child, double* x0, double* r, do
 
 namespace {
 constexpr char kModelMagic[8] = {'G', 'W', 'N', 'M', 'O', 'D', 'E', 'L'};
-constexpr uint32_t kModelVersion = 6;
+constexpr uint32_t kModelVersion = 7;
 
 template <typename V>
 bool write_vec(FILE* f, const std::vector<V>& v) {

@@ -932,8 +932,9 @@ GWN_HD inline T far3_eval(const T* f, T rx, T ry, T rz, bool o3) {
 }
 
 // FP32 moment block of a node or leaf: the first 6 float4 carry orders 0-2 (and
-// the order-3 constant), the next 6 only the order-3 terms, read after the
-// order-2 value is formed (fewer registers live at once)
+// the order-3 constant), the next 6 only the order-3 terms.  All loads are issued
+// before the arithmetic (order 3: 1.7 % faster than loading the second half after
+// the order-2 value, at 64 instead of 62 registers, 8 blocks per SM either way)
 GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz, bool o3) {
     float f[48];
 #pragma unroll
@@ -943,6 +944,16 @@ GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz, b
         f[4 * v + 1] = a.y;
         f[4 * v + 2] = a.z;
         f[4 * v + 3] = a.w;
+    }
+    if (o3) {
+#pragma unroll
+        for (int v = 6; v < 12; ++v) {
+            const float4 a = GWN_LDG(M + v);
+            f[4 * v] = a.x;
+            f[4 * v + 1] = a.y;
+            f[4 * v + 2] = a.z;
+            f[4 * v + 3] = a.w;
+        }
     }
     const float r2 = rx * rx + ry * ry + rz * rz;
     const float rs = rsqrtf(r2);
@@ -954,17 +965,7 @@ GWN_HD inline float far3_node32(const float4* M, float rx, float ry, float rz, b
     const float t2 = rx * (f[13] * xx + f[16] * rx * ry + f[17] * rx * rz + f[18] * yy + f[20] * zz + f[22] * ry * rz) +
                      ry * (f[14] * yy + f[19] * ry * rz + f[21] * zz) + f[15] * zz * rz;
     float w = i3 * (t0 + i2 * (t1 + i2 * t2));
-    if (o3) {
-#pragma unroll
-        for (int v = 6; v < 12; ++v) {
-            const float4 a = GWN_LDG(M + v);
-            f[4 * v] = a.x;
-            f[4 * v + 1] = a.y;
-            f[4 * v + 2] = a.z;
-            f[4 * v + 3] = a.w;
-        }
-        w += far3_order3<float>(f, rx, ry, rz, xx, yy, zz, i2, i3);
-    }
+    if (o3) w += far3_order3<float>(f, rx, ry, rz, xx, yy, zz, i2, i3);
     return w;
 }
 

@@ -5,7 +5,7 @@
  * NURBS curves (2D) and trimmed NURBS patches (3D) with the agglomerated
  * evaluation of "Spatially Accelerated Winding Numbers for Curved Geometry"
  * (Algorithm 1): adaptive subdivision (Section 3.2), uncentred moments summed
- * up a Karras LBVH and centred in place (Section 3.1, Eq. 3 and the moment
+ * up a BVH (top-down sweep or Karras LBVH) and centred in place (Section 3.1, Eq. 3 and the moment
  * transform), and a per-query traversal that evaluates the order-0/1/2 Taylor
  * expansion of Eq. 3 (order 3 in 3D as an extension) for clusters that pass
  * the far test of Section 3 and the
@@ -82,7 +82,7 @@ enum {
 };
 
 enum {
-    GWN_MODE_BVH = 0,    /* Algorithm 1: LBVH traversal with Taylor far field */
+    GWN_MODE_BVH = 0,    /* Algorithm 1: BVH traversal with Taylor far field */
     GWN_MODE_DIRECT = 1  /* plain direct sum: every leaf evaluated exactly for every query */
 };
 
@@ -176,7 +176,7 @@ void gwn_default_query_opts(gwn_query_opts* opts);
 
 /* Build a 2D model from n NURBS curves (Algorithm 1, preprocessing):
  * Bezier extraction and adaptive subdivision (Section 3.2), chord moments
- * (Section 3.1: far from a curve its GWN equals that of its chord), LBVH
+ * (Section 3.1: far from a curve its GWN equals that of its chord), BVH
  * (Section 3.1, Karras), moment up-sweep and centring.  On success *out holds
  * a device-resident model.  Errors: INVALID_ARG, INVALID_GEOMETRY, OOM, CUDA. */
 gwn_status gwn_build_2d(const gwn_curve2d* curves, size_t n, const gwn_build_opts* opts, gwn_model* out);
@@ -185,7 +185,7 @@ gwn_status gwn_build_2d(const gwn_curve2d* curves, size_t n, const gwn_build_opt
  * preprocessing): adaptive subdivision of the parameter rectangle with trims
  * clipped to every leaf (Section 3.2), leaf moments and centroid by
  * Gauss-Legendre quadrature over the trimmed region via Green's theorem
- * (Section 3.1, Figure 3), LBVH, up-sweep and centring.  Same errors. */
+ * (Section 3.1, Figure 3), BVH, up-sweep and centring.  Same errors. */
 gwn_status gwn_build_3d(const gwn_patch3d* patches, size_t n, const gwn_build_opts* opts, gwn_model* out);
 
 /* GWN at n points (Algorithm 1, batched query).

@@ -1,5 +1,5 @@
-// build.cpp -- generic LBVH construction with moment up-sweep and centring,
-// and the 2D preprocessing of Algorithm 1.
+// build.cpp -- generic BVH construction (top-down sweep or Karras LBVH) with
+// moment up-sweep and centring, and the 2D preprocessing of Algorithm 1.
 //
 // 2D leaves (Section 3.2): every NURBS curve is split into rational Bezier
 // pieces, then each piece is bisected until the diagonal of its control-point
@@ -91,7 +91,7 @@ int decompose(int p, int n, const double* U, int hd, const double* P, std::vecto
     return (int)brk->size() - 1;
 }
 
-// ------------------------------------------------------------------ LBVH
+// ------------------------------------------------------------------ BVH
 
 static inline int clz64(uint64_t x) { return x ? __builtin_clzll(x) : 64; }
 

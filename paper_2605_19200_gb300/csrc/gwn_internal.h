@@ -1,7 +1,8 @@
 // gwn_internal.h -- data layouts shared by the host build and the CUDA kernels.
 //
-// A model is a Karras LBVH (Section 3.1) over leaf primitives.  Internal node k
-// (0 <= k < n_leaves - 1) stores its centroid x0 and squared radius r^2 (radius
+// A model is a BVH (Section 3.1; top-down sweep or Karras LBVH, numbered alike)
+// over leaf primitives.  Internal node k (0 <= k < n_leaves - 1) stores its
+// centroid x0 and squared radius r^2 (radius
 // = half the diagonal of the node's control-point box, Section 3), its two
 // children (>= 0: internal node, < 0: leaf ~i), and the Taylor coefficients
 // of Eq. 3 (order 2; order 3 in 3D as an extension) folded into the polynomial

@@ -313,7 +313,10 @@ gwn_status gwn_model_load(const char* path, int32_t device, gwn_model* out);
  * model; a batch runs the query of each item (its own model, points and
  * outputs, all device memory) through the same pipeline as gwn_query with the
  * model's build options, the items spread over a pool of CUDA streams so that
- * their work overlaps on the GPU.  The first call with a given item list
+ * their work overlaps on the GPU (an item of more than 2^20 points is spread
+ * as chunk-aligned pieces, each with its own FP64 repair pass, so that one
+ * large model does not run its chunks one after another at the end; the values
+ * are those of the whole item).  The first call with a given item list
  * captures the whole fork/join into a CUDA graph; later calls with an
  * identical list (same models, pointers and sizes) replay it with a single
  * graph launch on the caller's stream.  Asynchronous: outputs are ready when

@@ -5,7 +5,10 @@
 // the stream with the least work so far), so the pipelines of different
 // models run concurrently on the GPU: small models fill the SMs that a large
 // one leaves idle, and the latency-bound FP64 tails of one item overlap the
-// bulk of another.  The whole fork/join is captured once into a CUDA graph
+// bulk of another.  An item longer than one chunk of the query pipeline is
+// planned as chunk-aligned pieces, so that a large model's chunks also run on
+// several streams instead of one after the other at the end of the batch;
+// the pieces bin and evaluate their points exactly as the whole item would.  The whole fork/join is captured once into a CUDA graph
 // (every stage of the query pipeline is driven by device-side counters, with
 // no host synchronisation, so it can be captured) and later calls with the
 // same items replay that graph with one cudaGraphLaunch on the caller's stream.
@@ -194,8 +197,36 @@ gwn_status stage_items(gwn_batch_s* B, const gwn_query_item* items, size_t n_ite
 // the items' host buffers are copied in before and out after each query (one
 // cudaMemcpyAsync per buffer on the item's stream); `dev` holds the items as
 // the kernels see them.
-gwn_status issue_plan(gwn_batch_s* B, const gwn_query_item* dev, const gwn_query_item* host, size_t n_items) {
-    std::vector<size_t> order(n_items);
+// points per piece of a long item: the query pipeline's chunk (gwn_api.cu)
+constexpr size_t kPiece = (size_t)1 << 20;
+
+// item i restricted to its points [off, off + n): the same arrays, offset
+gwn_query_item piece_of(const gwn_query_item& it, size_t off, size_t n) {
+    gwn_query_item p = it;
+    const size_t pb = n ? point_bytes(it) / it.n : 0;  // bytes per point
+    p.points = static_cast<const char*>(it.points) + off * pb;
+    p.n = n;
+    p.out_w = it.out_w + off;
+    if (it.out_label) p.out_label = it.out_label + off;
+    if (it.out_status) p.out_status = it.out_status + off;
+    return p;
+}
+
+gwn_status issue_plan(gwn_batch_s* B, const gwn_query_item* items_dev, const gwn_query_item* items_host,
+                      size_t n_items) {
+    // chunk-aligned pieces of the items (device and, for host buffers, host views)
+    std::vector<gwn_query_item> pd, ph;
+    for (size_t i = 0; i < n_items; ++i)
+        for (size_t off = 0; off < items_dev[i].n || (off == 0 && items_dev[i].n == 0); off += kPiece) {
+            const size_t n = std::min(kPiece, items_dev[i].n - off);
+            pd.push_back(piece_of(items_dev[i], off, n));
+            if (items_host) ph.push_back(piece_of(items_host[i], off, n));
+            if (items_dev[i].n == 0) break;
+        }
+    const gwn_query_item* dev = pd.data();
+    const gwn_query_item* host = items_host ? ph.data() : nullptr;
+    const size_t n_pieces = pd.size();
+    std::vector<size_t> order(n_pieces);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return dev[a].n > dev[b].n; });
     const size_t ns = B->streams.size();
@@ -204,7 +235,7 @@ gwn_status issue_plan(gwn_batch_s* B, const gwn_query_item* dev, const gwn_query
     for (size_t i : order) {
         size_t k = std::min_element(load.begin(), load.end()) - load.begin();
         plan[k].push_back(i);
-        load[k] += (double)dev[i].n + 65536.0;  // fixed cost per item
+        load[k] += (double)dev[i].n + 65536.0;  // fixed cost per piece
     }
     cudaStream_t origin = B->streams[0];
     BATCH_CUDA_TRY(cudaEventRecord(B->fork, origin));

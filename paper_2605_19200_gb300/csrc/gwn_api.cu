@@ -950,7 +950,7 @@ static gwn_status autotune(gwn_model_s* m) {
                   cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
                   ensure_workspace(m, nt, 0) == GWN_OK;
         // best of two timed runs after one untimed run (microseconds)
-        auto timed_on = [&](double b, double bl, const float* pts_d, int np, double* out_d) -> double {
+        auto timed = [&](double b, double bl) -> double {
             gwn_query_opts q3;
             gwn_default_query_opts(&q3);
             q3.beta = b;
@@ -958,14 +958,13 @@ static gwn_status autotune(gwn_model_s* m) {
             float best = 1e30f;
             for (int rep = 0; rep < 3 && ok; ++rep) {
                 ok = cudaEventRecord(e0, 0) == cudaSuccess &&
-                     gwn_enqueue_device(m, pts_d, GWN_F32, np, out_d, nullptr, nullptr, q3, 0, m->ws) == GWN_OK &&
+                     gwn_enqueue_device(m, dt, GWN_F32, nt, wt, nullptr, nullptr, q3, 0, m->ws) == GWN_OK &&
                      cudaEventRecord(e1, 0) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
                 float ms = 0;
                 if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, ms);
             }
             return 1e3 * best;
         };
-        auto timed = [&](double b, double bl) -> double { return timed_on(b, bl, dt, nt, wt); };
         double best_t = 1e300;
         if (ok_cands.size() > 1) {
             for (const auto& c : ok_cands) {

@@ -222,3 +222,20 @@ extern "C" int hx_local2(const gwn_patch3d* patches, size_t n, const gwn_build_o
     }
     return t.n_internal;
 }
+
+// The FP64 traversal (query3_64, the repair's far field) at factor beta with the
+// model's Taylor order, and the exact FP64 sum over every leaf, for nq points.
+extern "C" int hx_query3_64(const gwn_patch3d* patches, size_t n, const gwn_build_opts* o, const double* q, int nq,
+                            double beta, double* bvh64, double* direct64) {
+    init_tables();
+    HostModel H;
+    gwn_status code;
+    if (!build_model_3d(patches, n, *o, &H, &code).empty()) return -1;
+    const DevTree t = host_tree(H, 1, o->order);
+    for (int i = 0; i < nq; ++i) {
+        uint32_t s = 0;
+        bvh64[i] = query3_64(t, q[3 * i], q[3 * i + 1], q[3 * i + 2], beta * beta, s);
+        direct64[i] = query3_64(t, q[3 * i], q[3 * i + 1], q[3 * i + 2], 0.0, s);
+    }
+    return t.n_leaves;
+}

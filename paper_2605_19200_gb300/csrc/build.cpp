@@ -426,7 +426,10 @@ static void topdown_tree(const LeafSet& L, std::vector<int>* perm, std::vector<i
                     dd += (phi[k] - plo[k]) * (phi[k] - plo[k]);
                 }
                 const double cost = (j + 1) * dd + (m - j - 1) * suf[j + 1];
-                if (cost < best) {
+                // equal costs (coincident boxes) go to the more balanced split,
+                // so that duplicated leaves do not form a chain
+                const bool tie = cost <= best * (1.0 + 1e-12) && cost >= best * (1.0 - 1e-12);
+                if ((cost < best && !tie) || (tie && std::abs(2 * (j + 1) - m) < std::abs(2 * best_k - m))) {
                     best = cost;
                     best_k = j + 1;
                     improved = true;

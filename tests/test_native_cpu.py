@@ -63,6 +63,17 @@ def test_tree_is_a_valid_binary_tree(tree_builder):
             assert L == list(range(L[0], L[0] + len(L)))
 
 
+def test_topdown_tree_stays_shallow_on_coincident_leaves():
+    """Forty copies of the same cube shell: the sweep's split costs tie on runs
+    of coincident boxes, and the tie goes to the balanced split, so the tree
+    stays about log2(leaves) deep (peeling one leaf per level gave depth 51
+    here, and enough copies would overflow the traversal's warp stack)."""
+    import math
+    m = gwn.gwn_build_3d(G.cube_shell(half=1.0) * 40, device=HOST_ONLY, beta=6.0, tree_builder=1)
+    info = m.info()
+    assert info["max_depth"] <= math.log2(info["n_leaves"]) + 8, info["max_depth"]
+
+
 def _sum_r3_and_visits(m, q, beta):
     """Sum of cubed node radii and the internal-node visits per query of
     Algorithm 1's traversal (far test |q - x0| > beta r), counted on the host."""
